@@ -1,0 +1,196 @@
+/*
+ * ltl.h -- C ABI of the GB300 enumerative LTL learner (sm_103a).
+ *
+ * The library learns a minimal LTL formula separating positive from negative
+ * finite traces ("LTL learning on GPUs", arXiv 2402.12373): bottom-up,
+ * size-by-size enumeration over !, &, |, X, F, G and U (Section 3, the
+ * `enum` / `handleOp` / check-and-cache steps), each formula represented by
+ * its characteristic matrix of bit-vectors (Section 4), F, G and U computed
+ * by exponential propagation in O(log n) shifts (Section 4, Appendix B), and
+ * every candidate deduplicated exactly by observational equivalence modulo the
+ * suffixes of the input traces (Section 5 with an exact, not relaxed, check).
+ *
+ * Conventions shared by every entry point
+ *  - Traces.  A trace is a finite string over the powerset of the alphabet
+ *    {p0 .. p(n_props-1)}, n_props <= 32 (Section 2).  Position i of a trace
+ *    is one uint32: bit p set iff p holds there.  A trace set is `letters`
+ *    (all positions of all traces, concatenated) plus `offsets` (n_traces+1
+ *    non-decreasing prefix offsets, offsets[0] == 0).  Empty traces are legal
+ *    and satisfy no formula (every formula is false at i >= |tr|, Section 2).
+ *  - Characteristic sequences.  Bit t of word w of a trace's sequence is
+ *    position 64*w + t (least significant bit = position 0); positions at or
+ *    beyond the trace's length are always 0.  A trace of length L uses
+ *    ceil(L / 64) words.
+ *  - Formula text.  Fully parenthesised infix: `p3`, `!f`, `X f`, `F f`,
+ *    `G f`, `(f & g)`, `(f | g)`, `(f U g)`; extra parentheses `(f)` and
+ *    whitespace are accepted on input.
+ *  - Connective masks: LTL_NOT | LTL_AND | ... ; LTL_ALL selects all seven.
+ *  - Ownership.  The caller owns every buffer it passes; the library copies
+ *    what it needs and never keeps a caller pointer past the call (except
+ *    `ltl_opts.workspace`, which a context uses until it is destroyed).
+ *  - Errors.  No call returns silently: a CUDA error gives LTL_ERR_CUDA and
+ *    leaves the context usable; LTL_ERR_BUFSIZE reports a too-small output
+ *    buffer (the required size is written where stated).
+ *  - Threads.  A context may be used by one host thread at a time.
+ */
+#ifndef LTL_GB300_H
+#define LTL_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LTL_OK = 0,            /* a separating formula was found                  */
+    LTL_NOT_FOUND = 1,     /* none up to max_size (or P and N intersect)      */
+    LTL_CAP_REACHED = 2,   /* the language cache filled its memory first      */
+    LTL_ERR_INVALID = -1,  /* bad argument, malformed traces or formula       */
+    LTL_ERR_CUDA = -2,     /* a CUDA call failed (message: ltl_last_error)    */
+    LTL_ERR_OOM = -3,      /* workspace / allocator could not supply memory   */
+    LTL_ERR_TIMEOUT = -4,  /* a bounded device wait ran out (see spin_limit)  */
+    LTL_ERR_BUFSIZE = -5   /* output buffer too small                         */
+} ltl_status;
+
+enum {
+    LTL_NOT = 1, LTL_AND = 2, LTL_OR = 4, LTL_X = 8,
+    LTL_F = 16, LTL_G = 32, LTL_U = 64, LTL_ALL = 127
+};
+
+/* stop_on_solution values */
+enum {
+    LTL_STOP_NONE = 0,     /* enumerate every level up to max_size           */
+    LTL_STOP_FIRST = 1,    /* return at the first separating candidate       */
+    LTL_STOP_LEVEL = 2     /* finish the level where a separator was found   */
+};
+
+typedef struct {
+    const uint32_t *letters;   /* concatenated positions (host memory)        */
+    const uint64_t *offsets;   /* n_traces + 1 prefix offsets (host memory)   */
+    uint64_t n_traces;
+} ltl_traces;
+
+/* Options; a NULL pointer or a zero field selects the default. */
+typedef struct {
+    uint64_t mem_budget_bytes;   /* device bytes for cache + hash set; default:
+                                    workspace_bytes, else 40% of free memory  */
+    int stop_on_solution;        /* LTL_STOP_*, default LTL_STOP_FIRST when the
+                                    whole struct is absent                    */
+    uint64_t spin_limit;         /* bound on any device wait loop (iterations,
+                                    about 1 us each);
+                                    default 1 << 20                           */
+    void *(*alloc)(size_t bytes, void *stream, void *user); /* optional device
+                                    allocator (e.g. a framework's caching one) */
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;                  /* passed back to alloc / free               */
+    void *stream;                /* cudaStream_t to run on; NULL: the
+                                    context creates its own stream           */
+    void *workspace;             /* optional caller-owned device buffer used
+                                    for all device state (>= 256-byte aligned) */
+    uint64_t workspace_bytes;
+    const char *autotune_path;   /* reserved, may be NULL                     */
+} ltl_opts;
+
+#define LTL_MAX_LEVELS 64
+
+/* Per-level statistics.  Unique counts of a level are exact only when the
+ * level completed (levels 1 .. levels_done). */
+typedef struct {
+    int levels_done;                      /* last fully enumerated size level   */
+    int found_size;                       /* size of the returned formula, or 0 */
+    uint64_t unique[LTL_MAX_LEVELS];      /* new characteristic matrices by size */
+    uint64_t candidates[LTL_MAX_LEVELS];  /* candidates built at each size      */
+    double ms[LTL_MAX_LEVELS];            /* device time of each level's kernel */
+    uint64_t entries;                     /* language-cache entries at the end  */
+    uint64_t n_traces;                    /* |P| + |N|                          */
+    uint32_t words_per_trace;             /* characteristic words per trace     */
+    uint32_t threads_per_cta;             /* launch shape chosen               */
+    uint32_t traces_per_thread;
+    uint32_t chunk_groups;                /* 1: candidates kept in registers   */
+    uint64_t launches;                    /* kernels launched by the call       */
+    uint64_t h2d_bytes, d2h_bytes;        /* host<->device bytes copied         */
+    uint64_t max_entries;                 /* cache capacity in entries          */
+    double total_ms;                      /* wall time of the call              */
+} ltl_stats;
+
+/* ---------------------------------------------------------------------------
+ * ltl_learn -- learn a minimal separating formula (Section 2, the LTL learning
+ * problem; Section 3, `enum`).
+ *   P, N       positive and negative traces (host memory).  P and N should be
+ *              disjoint; a trace in both makes the problem unsolvable and the
+ *              result is LTL_NOT_FOUND.
+ *   n_props    alphabet size, 1..32; every letter must be < 2^n_props.
+ *   ops        connectives allowed (mask of LTL_NOT .. LTL_U).
+ *   max_size   largest formula size (syntax-tree nodes) tried, 1..63.
+ *   opts       may be NULL.
+ *   formula_out, formula_cap  receive the NUL-terminated text of a separating
+ *              formula of minimal size (any one of them; "" when none).  A
+ *              capacity of 8 * max_size + 1 bytes always suffices; a smaller
+ *              buffer that cannot hold the text gives LTL_ERR_BUFSIZE.
+ *   stats      may be NULL.
+ * Returns LTL_OK, LTL_NOT_FOUND, LTL_CAP_REACHED or an error.
+ * -------------------------------------------------------------------------*/
+ltl_status ltl_learn(const ltl_traces *P, const ltl_traces *N, int n_props, uint32_t ops,
+                     int max_size, const ltl_opts *opts, char *formula_out, size_t formula_cap,
+                     ltl_stats *stats);
+
+/* ---------------------------------------------------------------------------
+ * ltl_eval -- characteristic sequences of a formula over traces (Section 4,
+ * the characteristic matrix; F, G and U by exponential propagation).
+ *   formula          text as above; atoms must be < n_props.
+ *   traces           host memory.
+ *   cs_out           host buffer of n_traces * words_per_trace uint64, trace
+ *                    major: word w of trace t at cs_out[t * words_per_trace + w].
+ *   words_per_trace  must be >= ceil(max trace length / 64).
+ * -------------------------------------------------------------------------*/
+ltl_status ltl_eval(const char *formula, const ltl_traces *traces, int n_props,
+                    uint64_t *cs_out, int words_per_trace);
+
+/* ---------------------------------------------------------------------------
+ * Contexts: reusable device state (stream, workspace, language cache).  After
+ * a learn call the context keeps the enumerated cache until the next call, so
+ * it can be inspected.
+ * -------------------------------------------------------------------------*/
+typedef struct ltl_ctx ltl_ctx;
+
+ltl_status ltl_ctx_create(const ltl_opts *opts, ltl_ctx **out);
+void ltl_ctx_destroy(ltl_ctx *ctx);
+
+/* As ltl_learn, on a context (host traces). */
+ltl_status ltl_ctx_learn(ltl_ctx *ctx, const ltl_traces *P, const ltl_traces *N, int n_props,
+                         uint32_t ops, int max_size, char *formula_out, size_t formula_cap,
+                         ltl_stats *stats);
+
+/* As ltl_ctx_learn with the traces already in device memory: d_letters and
+ * d_offsets describe n_pos positive traces followed by n_neg negative ones;
+ * max_len must be >= the longest trace.  The device buffers are only read
+ * during the call. */
+ltl_status ltl_ctx_learn_device(ltl_ctx *ctx, const uint32_t *d_letters, const uint64_t *d_offsets,
+                                uint64_t n_pos, uint64_t n_neg, uint32_t max_len, int n_props,
+                                uint32_t ops, int max_size, char *formula_out, size_t formula_cap,
+                                ltl_stats *stats);
+
+/* Entries of size level `level` of the last learn call are the cache indices
+ * [*begin, *begin + *count). */
+ltl_status ltl_ctx_level_range(ltl_ctx *ctx, int level, uint64_t *begin, uint64_t *count);
+
+/* Formula text and characteristic matrix of cache entry `idx` of the last
+ * learn call.  cs_out (host, may be NULL) receives n_traces * words_per_trace
+ * uint64 in the layout of ltl_eval; words_per_trace must equal
+ * stats.words_per_trace of that call.  LTL_ERR_BUFSIZE if formula_cap is too
+ * small. */
+ltl_status ltl_ctx_entry(ltl_ctx *ctx, uint64_t idx, char *formula_out, size_t formula_cap,
+                         uint64_t *cs_out, int words_per_trace);
+
+/* Message of the last error on this host thread (static storage). */
+const char *ltl_last_error(void);
+
+/* Library build information (static storage). */
+const char *ltl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LTL_GB300_H */

@@ -1,0 +1,276 @@
+"""ctypes binding of libltl_gb300.so (argument marshalling only).
+
+Every step of learning and evaluation runs in the library's CUDA kernels;
+this module only converts Python / numpy / torch objects into the C ABI of
+include/ltl.h.  PyTorch supplies device memory (the workspace tensor) and the
+CUDA stream.  There is no fallback: if the shared library cannot be loaded the
+import fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+LTL_OK, LTL_NOT_FOUND, LTL_CAP_REACHED = 0, 1, 2
+LTL_ERR_INVALID, LTL_ERR_CUDA, LTL_ERR_OOM, LTL_ERR_TIMEOUT, LTL_ERR_BUFSIZE = -1, -2, -3, -4, -5
+STATUS = {0: "found", 1: "not_found", 2: "cap", -1: "invalid", -2: "cuda", -3: "oom", -4: "timeout",
+          -5: "bufsize"}
+NOT, AND, OR, X, F, G, U, ALL = 1, 2, 4, 8, 16, 32, 64, 127
+STOP_NONE, STOP_FIRST, STOP_LEVEL = 0, 1, 2
+MAX_LEVELS = 64
+
+# Every symbol include/ltl.h declares.
+EXPORTS = ["ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_destroy", "ltl_ctx_learn",
+           "ltl_ctx_learn_device", "ltl_ctx_level_range", "ltl_ctx_entry", "ltl_last_error",
+           "ltl_version"]
+
+
+class LtlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Traces(ctypes.Structure):
+    _fields_ = [("letters", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n_traces", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("stop_on_solution", ctypes.c_int),
+                ("spin_limit", ctypes.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("user", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_uint64), ("autotune_path", ctypes.c_char_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("levels_done", ctypes.c_int), ("found_size", ctypes.c_int),
+                ("unique", ctypes.c_uint64 * MAX_LEVELS), ("candidates", ctypes.c_uint64 * MAX_LEVELS),
+                ("ms", ctypes.c_double * MAX_LEVELS), ("entries", ctypes.c_uint64),
+                ("n_traces", ctypes.c_uint64), ("words_per_trace", ctypes.c_uint32),
+                ("threads_per_cta", ctypes.c_uint32), ("traces_per_thread", ctypes.c_uint32),
+                ("chunk_groups", ctypes.c_uint32), ("launches", ctypes.c_uint64),
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+    def to_dict(self, max_size: int) -> Dict:
+        K = max_size
+        return {
+            "levels_done": self.levels_done, "found_size": self.found_size,
+            "unique": [int(self.unique[c]) for c in range(K + 1)],
+            "candidates": [int(self.candidates[c]) for c in range(K + 1)],
+            "ms": [float(self.ms[c]) for c in range(K + 1)],
+            "entries": int(self.entries), "n_traces": int(self.n_traces),
+            "words_per_trace": int(self.words_per_trace), "threads_per_cta": int(self.threads_per_cta),
+            "traces_per_thread": int(self.traces_per_thread), "chunk_groups": int(self.chunk_groups),
+            "launches": int(self.launches), "h2d_bytes": int(self.h2d_bytes),
+            "d2h_bytes": int(self.d2h_bytes), "max_entries": int(self.max_entries),
+            "total_ms": float(self.total_ms),
+        }
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libltl_gb300.so is missing; run paper_2402_12373_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, u64, i32, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+    TP = ctypes.POINTER(Traces)
+    L.ltl_learn.argtypes = [TP, TP, i32, u32, i32, ctypes.POINTER(Opts), ctypes.c_char_p, ctypes.c_size_t,
+                            ctypes.POINTER(Stats)]
+    L.ltl_eval.argtypes = [ctypes.c_char_p, TP, i32, vp, i32]
+    L.ltl_ctx_create.argtypes = [ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    L.ltl_ctx_destroy.argtypes = [vp]
+    L.ltl_ctx_destroy.restype = None
+    L.ltl_ctx_learn.argtypes = [vp, TP, TP, i32, u32, i32, ctypes.c_char_p, ctypes.c_size_t,
+                                ctypes.POINTER(Stats)]
+    L.ltl_ctx_learn_device.argtypes = [vp, vp, vp, u64, u64, u32, i32, u32, i32, ctypes.c_char_p,
+                                       ctypes.c_size_t, ctypes.POINTER(Stats)]
+    L.ltl_ctx_level_range.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    L.ltl_ctx_entry.argtypes = [vp, u64, ctypes.c_char_p, ctypes.c_size_t, vp, i32]
+    L.ltl_last_error.restype = ctypes.c_char_p
+    L.ltl_version.restype = ctypes.c_char_p
+    for f in ("ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_learn", "ltl_ctx_learn_device",
+              "ltl_ctx_level_range", "ltl_ctx_entry"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return load().ltl_last_error().decode(errors="replace")
+
+
+def _check(rc: int, ok=(LTL_OK, LTL_NOT_FOUND, LTL_CAP_REACHED)) -> int:
+    if rc not in ok:
+        raise LtlError(rc, last_error())
+    return rc
+
+
+class _HostTraces:
+    """Keeps numpy arrays alive while a ctypes Traces struct points at them."""
+
+    def __init__(self, ts):
+        self.letters = np.ascontiguousarray(np.asarray(ts.letters, dtype=np.uint32))
+        self.offsets = np.ascontiguousarray(np.asarray(ts.offsets, dtype=np.uint64))
+        if self.letters.size == 0:
+            self.letters = np.zeros(1, dtype=np.uint32)
+        self.struct = Traces(self.letters.ctypes.data, self.offsets.ctypes.data, self.offsets.shape[0] - 1)
+
+
+def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int = 0,
+          spin_limit: int = 0) -> Opts:
+    o = Opts()
+    o.mem_budget_bytes = int(mem_budget)
+    o.stop_on_solution = int(stop)
+    o.spin_limit = int(spin_limit)
+    o.alloc = ALLOC_FN()
+    o.free = FREE_FN()
+    o.user = None
+    o.stream = stream
+    o.workspace = None
+    o.workspace_bytes = 0
+    o.autotune_path = None
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def default_workspace(nbytes: Optional[int] = None, device: int = 0):
+    """A torch-allocated device workspace (uint8 tensor, 256-byte aligned)."""
+    import torch
+    if nbytes is None:
+        free, _ = torch.cuda.mem_get_info(device)
+        nbytes = int(free * 0.4)
+    return torch.empty(int(nbytes), dtype=torch.uint8, device="cuda:%d" % device)
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """A reusable learner context: stream + torch workspace + last cache."""
+
+    def __init__(self, workspace=None, stop: int = STOP_FIRST, stream=None, mem_budget: int = 0,
+                 spin_limit: int = 0, workspace_bytes: Optional[int] = None):
+        self._L = load()
+        if workspace is None:
+            workspace = default_workspace(workspace_bytes)
+        self.workspace = workspace
+        if stream is None:
+            stream = _current_stream()
+        self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit)
+        h = ctypes.c_void_p()
+        _check(self._L.ltl_ctx_create(ctypes.byref(self._opts), ctypes.byref(h)), ok=(LTL_OK,))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ltl_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def learn(self, P, N, n_props: int, ops: int = ALL, max_size: int = 7) -> Dict:
+        hp, hn = _HostTraces(P), _HostTraces(N)
+        buf = ctypes.create_string_buffer(8 * max_size + 64)
+        st = Stats()
+        rc = self._L.ltl_ctx_learn(self._h, ctypes.byref(hp.struct), ctypes.byref(hn.struct), n_props, ops,
+                                   max_size, buf, len(buf), ctypes.byref(st))
+        return _result(_check(rc), buf, st, max_size)
+
+    def learn_device(self, letters, offsets, n_pos: int, n_neg: int, max_len: int, n_props: int,
+                     ops: int = ALL, max_size: int = 7) -> Dict:
+        """Traces already on the device: torch uint32/int32 letters, int64 offsets."""
+        buf = ctypes.create_string_buffer(8 * max_size + 64)
+        st = Stats()
+        rc = self._L.ltl_ctx_learn_device(self._h, ctypes.c_void_p(letters.data_ptr()),
+                                          ctypes.c_void_p(offsets.data_ptr()), n_pos, n_neg, max_len, n_props,
+                                          ops, max_size, buf, len(buf), ctypes.byref(st))
+        return _result(_check(rc), buf, st, max_size)
+
+    def level_range(self, level: int):
+        b, c = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._L.ltl_ctx_level_range(self._h, level, ctypes.byref(b), ctypes.byref(c)), ok=(LTL_OK,))
+        return int(b.value), int(c.value)
+
+    def entry(self, idx: int, n_traces: int, words_per_trace: int):
+        buf = ctypes.create_string_buffer(1024)
+        cs = np.zeros((max(n_traces, 1), words_per_trace), dtype=np.uint64)
+        _check(self._L.ltl_ctx_entry(self._h, idx, buf, len(buf), cs.ctypes.data, words_per_trace),
+               ok=(LTL_OK,))
+        return buf.value.decode(), cs[:n_traces]
+
+
+def _result(rc: int, buf, st: Stats, max_size: int) -> Dict:
+    d = st.to_dict(max_size)
+    d["status"] = STATUS[rc]
+    d["formula"] = buf.value.decode() if rc == LTL_OK else None
+    d["size"] = d["found_size"] if rc == LTL_OK else None
+    return d
+
+
+def learn(P, N, n_props: int, ops: int = ALL, max_size: int = 7, stop: int = STOP_FIRST,
+          workspace=None, mem_budget: int = 0) -> Dict:
+    """One-shot ltl_learn with host traces (TraceSet-like P and N)."""
+    L = load()
+    hp, hn = _HostTraces(P), _HostTraces(N)
+    o = _opts(stop, workspace, _current_stream() if workspace is not None else None, mem_budget)
+    buf = ctypes.create_string_buffer(8 * max_size + 64)
+    st = Stats()
+    rc = L.ltl_learn(ctypes.byref(hp.struct), ctypes.byref(hn.struct), n_props, ops, max_size,
+                     ctypes.byref(o), buf, len(buf), ctypes.byref(st))
+    return _result(_check(rc), buf, st, max_size)
+
+
+def evaluate(formula: str, traces, n_props: int, words_per_trace: Optional[int] = None) -> np.ndarray:
+    """ltl_eval: uint64 [n_traces, words_per_trace] characteristic sequences."""
+    L = load()
+    ht = _HostTraces(traces)
+    n = ht.offsets.shape[0] - 1
+    lens = np.diff(ht.offsets.astype(np.int64)) if n else np.zeros(0, np.int64)
+    W = max(1, (int(max(lens.max(), 0)) + 63) // 64) if n else 1
+    if words_per_trace is None:
+        words_per_trace = W
+    out = np.zeros((max(n, 1), words_per_trace), dtype=np.uint64)
+    rc = L.ltl_eval(formula.encode(), ctypes.byref(ht.struct), n_props, out.ctypes.data, words_per_trace)
+    _check(rc, ok=(LTL_OK,))
+    return out[:n]
+
+
+def version() -> str:
+    return load().ltl_version().decode()
