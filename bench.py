@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 enumerative LTL learner.
+
+Workload (the single-large learning problem): 3 propositions, 1024 positive +
+1024 negative seeded synthetic traces of length U{16..32}, Bernoulli(0.3)
+proposition bits, labelled by the planted formula (G(!p0 | F p1) | p2); all
+seven connectives; sizes 1..9, every level enumerated completely
+(enumeration-only mode), the language cache and hash set resident in HBM.
+
+One step = one whole learn call (trace packing, then every size level's
+candidate kernel, reading back the control block after each level).
+
+Metric: candidates x traces per second = sum over completed size levels of
+(candidates built at that size) * |P u N|, divided by the step's device time.
+
+  value    traces already resident in HBM (ltl_ctx_learn_device), CUDA events
+           on the library's stream around each step; L2 flushed between steps.
+  e2e      the same metric through ltl_ctx_learn with HOST trace buffers: the
+           host->device copy of the traces and the device->host reads of the
+           control block and formula are inside the wall-clock timed region.
+  roofline the dominant kernel (the level kernel of the largest size level):
+           algorithmic bytes / its event-timed duration vs measured HBM peak.
+  cpu_baseline  the plain C oracle, single-threaded, on a bounded sample.
+
+`--impl reference` times the oracle alone (the CPU reference of this
+workload) with the same metric.  With torchrun (N > 1) every rank learns its
+own independent problem (seed = rank); there is no collective on the path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "candidates×traces/s"
+MAX_SIZE = 9
+WORKLOAD = ("single_large: 3 props, 1024+1024 traces, length U{16..32}, Bernoulli(0.3) bits, "
+            "planted (G(!p0 | F p1) | p2), all 7 connectives, sizes 1..9 enumerated completely")
+N_UNARY = 4   # !, X, F, G
+
+
+def units_of(stats, T):
+    d = stats["levels_done"]
+    return sum(stats["candidates"][k] for k in range(1, d + 1)) * T
+
+
+def level_bytes(stats, k, T, W, n_props):
+    """Algorithmic HBM bytes of level k's launch: every candidate reads its
+    operand matrices and either writes its matrix (new) or reads one for the
+    full compare (duplicate): (operands + 1) * 8 * W bytes per trace."""
+    cand = stats["candidates"][k]
+    if k == 1:
+        unary, binary = cand, 0
+    else:
+        unary = min(cand, N_UNARY * stats["unique"][k - 1])
+        binary = cand - unary
+    return (unary * 2 + binary * 3) * T * W * 8
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    for f in ("ltl_kernels.cu", "ltl_device.cuh", "ltl_types.h"):
+        with open(os.path.join(ROOT, "paper_2402_12373_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def profiled_traffic(sha):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "level_kernel_single_large.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("kernel_sources_sha") == sha:
+            return d.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(target_s: float = 12.0, max_size: int = 6):
+    """The oracle as it stands (single-threaded C) on the same workload,
+    sizes 1..max_size enumerated completely, repeated for ~target_s."""
+    from oracle import oracle as O
+    from paper_2402_12373_gb300 import synth
+    spec = synth.single_large()
+    T = spec.n_traces
+    units = 0
+    secs = 0.0
+    runs = 0
+    while secs < target_s or runs == 0:
+        t0 = time.perf_counter()
+        r = O.learn(spec.P, spec.N, spec.n_props, max_size=max_size, stop_mode=0)
+        secs += time.perf_counter() - t0
+        units += sum(r["candidates"][1:max_size + 1]) * T
+        runs += 1
+    return {"value": units / secs, "unit": METRIC.split("/")[0] + "/s", "cores": 1, "kind": "oracle",
+            "sample": "single_large traces (2048), sizes 1..%d enumerated completely, %d run(s), %.1f s"
+                      % (max_size, runs, secs)}
+
+
+def run_reference(args):
+    from paper_2402_12373_gb300 import dist
+    rank, _, world = dist.env_rank()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2402_12373_gb300 import synth
+    spec = synth.single_large()
+    T = spec.n_traces
+    K = 5
+    for _ in range(args.warmup):
+        O.learn(spec.P, spec.N, spec.n_props, max_size=K, stop_mode=0)
+    units, secs = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.learn(spec.P, spec.N, spec.n_props, max_size=K, stop_mode=0)
+        secs += time.perf_counter() - t0
+        units += sum(r["candidates"][1:K + 1]) * T
+    value = units / secs
+    sample = "single_large traces (2048), sizes 1..%d enumerated completely per step (CPU oracle)" % K
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "reference_sample": sample, "n_traces": T},
+           "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--max-size", type=int, default=MAX_SIZE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ws-gb", type=float, default=0.0,
+                    help="workspace size in GB (default: half of the free device memory)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+
+    from paper_2402_12373_gb300 import _lib as L
+    from paper_2402_12373_gb300 import dist, synth
+
+    rank, local_rank, world = dist.env_rank()
+    torch.cuda.set_device(local_rank)
+    world = dist.init("nccl")
+    dev = torch.device("cuda", local_rank)
+
+    spec = synth.single_large(seed=rank)
+    T = spec.n_traces
+    letters = np.concatenate([spec.P.letters, spec.N.letters]).astype(np.int32)
+    offs = np.concatenate([spec.P.offsets, spec.N.offsets[1:] + spec.P.offsets[-1]]).astype(np.int64)
+    d_letters = torch.from_numpy(letters).to(dev)
+    d_offsets = torch.from_numpy(offs).to(dev)
+    max_len = spec.max_len()
+    K = args.max_size
+
+    free, _ = torch.cuda.mem_get_info(local_rank)
+    ws_bytes = int(args.ws_gb * 1e9) if args.ws_gb > 0 else int(free * 0.5)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = L.Context(workspace=ws, stop=L.STOP_NONE)
+
+    def step():
+        return ctx.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    gpu_idx = local_rank
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_idx = int(cvd.split(",")[local_rank])
+        except ValueError:
+            pass
+    results = []
+    times = []
+    with ClockSampler(gpu_idx) as clk:
+        dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            results.append(r)
+        torch.cuda.synchronize()
+        dist.barrier()
+    clocks = clk.summary()
+
+    total_ms = sum(times)
+    local_units = sum(units_of(r, T) for r in results)
+    max_ms = dist.reduce_max(total_ms, dev)
+    all_units = dist.reduce_sum(local_units, dev)
+    value = all_units / (max_ms / 1e3)
+    r0 = results[-1]
+    W = r0["words_per_trace"]
+
+    # dominant kernel: the level launch with the longest device time
+    kd = max(range(1, r0["levels_done"] + 1), key=lambda k: sum(r["ms"][k] for r in results))
+    kd_ms = statistics.mean(r["ms"][kd] for r in results)
+    kd_bytes = level_bytes(r0, kd, T, W, spec.n_props)
+    peaks, peak_src = measured_peaks()
+    achieved = kd_bytes / (kd_ms / 1e3) / 1e9
+    sha = kernel_sources_sha()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(sha),
+                "kernel": "level_kernel<W=%d>, size level %d" % (W, kd), "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": kd_bytes, "launch_ms": kd_ms,
+                "candidates_per_launch": r0["candidates"][kd], "kernel_sources_sha": sha}
+
+    # end to end: host trace buffers through ltl_ctx_learn
+    e2e_times, e2e_units, h2d, d2h = [], 0, 0, 0
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.learn(spec.P, spec.N, spec.n_props, max_size=K)
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_units += units_of(r, T)
+        h2d, d2h = r["h2d_bytes"], r["d2h_bytes"]
+    e2e_value = dist.reduce_sum(e2e_units, dev) / dist.reduce_max(sum(e2e_times), dev)
+
+    # time to learn (stop at the first separator), host buffers, wall clock
+    ctx_first = L.Context(workspace=ws, stop=L.STOP_FIRST)
+    ttl = []
+    found = None
+    for _ in range(5):
+        t0 = time.perf_counter()
+        r = ctx_first.learn(spec.P, spec.N, spec.n_props, max_size=K)
+        ttl.append(1e3 * (time.perf_counter() - t0))
+        found = r
+    ctx_first.close()
+
+    launches = sum(r["launches"] for r in results)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_traces": T, "words_per_trace": W, "max_size": K,
+                       "mode": "enumeration-only (every level complete)",
+                       "l2": "flushed between steps (512 MiB write); cache working set > L2",
+                       "parallelism": "independent problem per rank (seed = rank)" if world > 1 else "1 GPU",
+                       "launch": {"threads_per_cta": r0["threads_per_cta"],
+                                  "traces_per_thread": r0["traces_per_thread"],
+                                  "chunk_groups": r0["chunk_groups"]}},
+            "levels": {"unique": r0["unique"][1:], "candidates": r0["candidates"][1:],
+                       "ms": [round(x, 4) for x in r0["ms"][1:]], "entries": r0["entries"]},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "time_to_learn_ms": {"median": statistics.median(ttl), "size": found["size"],
+                                 "formula": found["formula"], "mode": "stop at first separator, host buffers"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
