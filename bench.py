@@ -69,7 +69,7 @@ def level_bytes(stats, k, T, W, n_props):
 
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for f in ("ltl_kernels.cu", "ltl_device.cuh", "ltl_types.h"):
+    for f in ("ltl_level_fused.cuh", "ltl_level_common.cuh", "ltl_device.cuh", "ltl_types.h"):
         with open(os.path.join(ROOT, "paper_2402_12373_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -78,9 +78,8 @@ typedef struct {
                                     workspace_bytes, else 40% of free memory  */
     int stop_on_solution;        /* LTL_STOP_*, default LTL_STOP_FIRST when the
                                     whole struct is absent                    */
-    uint64_t spin_limit;         /* bound on any device wait loop (iterations,
-                                    about 1 us each);
-                                    default 1 << 20                           */
+    uint64_t spin_limit;         /* bound on every device wait loop, in
+                                    iterations (about 1 us each); default 2^20 */
     void *(*alloc)(size_t bytes, void *stream, void *user); /* optional device
                                     allocator (e.g. a framework's caching one) */
     void (*free)(void *ptr, void *stream, void *user);
@@ -109,6 +108,8 @@ typedef struct {
     uint32_t threads_per_cta;             /* launch shape chosen               */
     uint32_t traces_per_thread;
     uint32_t chunk_groups;                /* 1: candidates kept in registers   */
+    uint32_t batch;                       /* candidates per CTA batch          */
+    uint32_t ctas_per_sm;                 /* resident CTAs per SM              */
     uint64_t launches;                    /* kernels launched by the call       */
     uint64_t h2d_bytes, d2h_bytes;        /* host<->device bytes copied         */
     uint64_t max_entries;                 /* cache capacity in entries          */

@@ -57,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("ms", ctypes.c_double * MAX_LEVELS), ("entries", ctypes.c_uint64),
                 ("n_traces", ctypes.c_uint64), ("words_per_trace", ctypes.c_uint32),
                 ("threads_per_cta", ctypes.c_uint32), ("traces_per_thread", ctypes.c_uint32),
-                ("chunk_groups", ctypes.c_uint32), ("launches", ctypes.c_uint64),
+                ("chunk_groups", ctypes.c_uint32), ("batch", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("launches", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
 
@@ -71,6 +72,7 @@ class Stats(ctypes.Structure):
             "entries": int(self.entries), "n_traces": int(self.n_traces),
             "words_per_trace": int(self.words_per_trace), "threads_per_cta": int(self.threads_per_cta),
             "traces_per_thread": int(self.traces_per_thread), "chunk_groups": int(self.chunk_groups),
+            "batch": int(self.batch), "ctas_per_sm": int(self.ctas_per_sm),
             "launches": int(self.launches), "h2d_bytes": int(self.h2d_bytes),
             "d2h_bytes": int(self.d2h_bytes), "max_entries": int(self.max_entries),
             "total_ms": float(self.total_ms),

@@ -1,6 +1,7 @@
 """Builds the in-tree CUDA library libltl_gb300.so for sm_103a with nvcc.
 
-Two translation units (kernels, host driver) are compiled in parallel and
+The translation units (two size-level kernels, the small kernels, the host
+driver) are compiled in parallel and
 linked into one shared library next to this file.  A rebuild happens only
 when a source or header is newer than the library.
 """
@@ -19,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libltl_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ltl_kernels.cu", "ltl_host.cu"]
+SOURCES = ["ltl_level_fused_w1.cu", "ltl_level_fused_w2.cu", "ltl_level_fused_w48.cu", "ltl_level_stream.cu",
+           "ltl_misc.cu", "ltl_host.cu"]
 
 
 def nvcc() -> str:
@@ -65,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         out, _ = p.communicate()
         outs.append(out.decode(errors="replace"))
         if p.returncode != 0:
-            raise RuntimeError("nvcc failed:\n%s\n%s" % (" ".join(cmd), out.decode(errors="replace")))
+            raise RuntimeError("nvcc failed:\n%s\n%s" % (" ".join(cmd), out.decode(errors="replace")[-6000:]))
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     subprocess.check_call(cmd)

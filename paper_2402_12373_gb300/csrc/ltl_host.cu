@@ -21,10 +21,14 @@
 #include "ltl_types.h"
 
 namespace ltl {
-const void *level_kernel_ptr(int W, int C);
-int level_kernel_max_threads(int W, int C);
-cudaError_t launch_level(int W, int C, int grid, int threads, const Problem &pb, const LevelArgs &la,
-                         cudaStream_t s);
+const void *fused_kernel_ptr_w1(int C, int op);
+const void *fused_kernel_ptr_w2(int C, int op);
+const void *fused_kernel_ptr_w48(int W, int C, int op);
+const void *stream_kernel_ptr(int W, int C);
+inline const void *fused_kernel_ptr(int W, int C, int op) {
+    return W == 1 ? fused_kernel_ptr_w1(C, op) : W == 2 ? fused_kernel_ptr_w2(C, op) : fused_kernel_ptr_w48(W, C, op);
+}
+inline int fused_batch(int W, int C) { return (W * C >= 8) ? 2 : 4; }
 cudaError_t launch_pack(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
                         int W, int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
                         cudaStream_t s);
@@ -206,7 +210,8 @@ size_t tokens_to_text(const uint32_t *tok, int n, int i, std::string &out) {
 // ------------------------------------------------------------------- context
 
 struct Layout {
-    int W = 0, Wt = 0, C = 0, NT = 0;
+    int W = 0, Wt = 0, C = 0, NT = 0, NB = 1;
+    size_t smem = 0;
     uint32_t G = 0;
     uint32_t n_traces = 0, n_pos = 0;
     int n_props = 0, nsteps = 0;
@@ -233,7 +238,13 @@ struct ltl_ctx {
     Layout L;
     bool have_result = false;
     uint64_t lvl_begin[kMaxLevels] = {}, lvl_count[kMaxLevels] = {};
-    int occ_W = -1, occ_C = -1, occ_NT = -1, occ_blocks = 0;
+    struct Occ {
+        const void *fn;
+        int nt;
+        size_t smem;
+        int blocks;
+    };
+    std::vector<Occ> occ;
 };
 
 namespace {
@@ -278,23 +289,30 @@ ltl_status plan(ltl_ctx *c, uint64_t n_pos, uint64_t n_neg, uint64_t max_len, ui
     L.Wt = (int)pow2_ceil((uint64_t)L.W);
     if (L.Wt > 8) return fail(LTL_ERR_INVALID, "traces longer than 512 positions are not supported by ltl_learn");
     L.nsteps = ceil_log2(max_len);
+    // Each thread holds C pairs of traces x W words (C * W <= 8) of a
+    // candidate; a CTA of up to 256 threads holds a whole matrix of up to
+    // 4096 / W traces (fused kernel), larger ones go through the two-pass
+    // streaming kernel in `G` chunk groups.
     const int Cmax = 8 / L.Wt;
-    const int maxNT = level_kernel_max_threads(L.Wt, Cmax);
+    const uint64_t maxNT = 256;
     const uint64_t pairs = std::max<uint64_t>(1, (T + 1) / 2);
-    if (pairs <= (uint64_t)maxNT * (uint64_t)Cmax) {
+    if (pairs <= maxNT * (uint64_t)Cmax) {
         uint64_t nt = pow2_ceil((pairs + Cmax - 1) / Cmax);
-        nt = std::min<uint64_t>(std::max<uint64_t>(nt, 32), (uint64_t)maxNT);
+        nt = std::min<uint64_t>(std::max<uint64_t>(nt, 32), maxNT);
         uint64_t cc = pow2_ceil((pairs + nt - 1) / nt);
         L.NT = (int)nt;
         L.C = (int)std::min<uint64_t>(cc, (uint64_t)Cmax);
         L.G = 1;
+        L.NB = fused_batch(L.Wt, L.C);
     } else {
-        L.NT = maxNT;
+        L.NT = (int)maxNT;
         L.C = Cmax;
-        L.G = (uint32_t)((pairs + (uint64_t)maxNT * Cmax - 1) / ((uint64_t)maxNT * Cmax));
+        L.G = (uint32_t)((pairs + maxNT * Cmax - 1) / (maxNT * Cmax));
+        L.NB = 1;
     }
     L.plane = (uint64_t)L.G * L.C * 2 * L.NT;
     L.stride = (uint64_t)L.Wt * L.plane;
+    L.smem = L.G == 1 ? (size_t)(L.NB + 1) * 8 * L.stride : 0;
 
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -347,32 +365,57 @@ ltl_status plan(ltl_ctx *c, uint64_t n_pos, uint64_t n_neg, uint64_t max_len, ui
     return LTL_OK;
 }
 
-int occupancy(ltl_ctx *c, int W, int C, int NT) {
-    if (c->occ_W == W && c->occ_C == C && c->occ_NT == NT) return c->occ_blocks;
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, level_kernel_ptr(W, C), NT, 0) != cudaSuccess) {
-        (void)cudaGetLastError();
-        b = 1;
-    }
-    c->occ_W = W; c->occ_C = C; c->occ_NT = NT; c->occ_blocks = std::max(b, 1);
-    return c->occ_blocks;
+const void *level_kernel_for(const Layout &L, int op) {
+    return L.G == 1 ? fused_kernel_ptr(L.Wt, L.C, op) : stream_kernel_ptr(L.Wt, L.C);
 }
 
-// Candidate space of size level k (Section 3, handleOp) as segments, in the
-// paper's connective order F, U, G, X, And, Or, Not.
-int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, Seg *segs, uint64_t &total) {
+// Resident CTAs per SM of a layout's kernel for one connective (dynamic
+// shared memory opted in); cached per kernel.
+ltl_status occupancy(ltl_ctx *c, const Layout &L, int op, int &blocks) {
+    const void *fn = level_kernel_for(L, op);
+    if (!fn) return fail(LTL_ERR_INVALID, "no kernel for W=%d C=%d", L.Wt, L.C);
+    for (const auto &e : c->occ)
+        if (e.fn == fn && e.nt == L.NT && e.smem == L.smem) {
+            blocks = e.blocks;
+            return LTL_OK;
+        }
+    if (L.smem > 0) CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    int b = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, L.NT, L.smem));
+    if (b < 1) return fail(LTL_ERR_INVALID, "level kernel cannot be resident (threads %d, smem %zu)", L.NT, L.smem);
+    c->occ.push_back({fn, L.NT, L.smem, b});
+    blocks = b;
+    return LTL_OK;
+}
+
+// Candidate space of size level k (Section 3, handleOp) as segments, grouped
+// by connective in the paper's order F, U, G, X, And, Or, Not.  Each group is
+// one launch; tile ids restart at 0 in every group.
+struct OpGroup {
+    int op;
+    int first, count;       // segments [first, first + count) of the level
+    uint64_t tiles;
+};
+
+int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, Seg *segs, OpGroup *groups, int &n_groups) {
     int n = 0;
-    total = 0;
+    n_groups = 0;
+    uint64_t total = 0;
     auto add = [&](Seg s) {
         s.tile_begin = total;
         total += s.n_tiles;
         segs[n++] = s;
+    };
+    auto close_group = [&](int op, int first) {
+        if (n > first) groups[n_groups++] = OpGroup{op, first, n - first, total};
+        total = 0;
     };
     if (k == 1) {
         Seg s{};
         s.op = OP_ATOM; s.kind = SEG_UNARY; s.a_begin = 0; s.a_count = (uint64_t)n_props;
         s.n_tiles = (s.a_count + kTileU - 1) / kTileU;
         add(s);
+        close_group(OP_ATOM, 0);
         return n;
     }
     const int order[7] = {OP_F, OP_U, OP_G, OP_X, OP_AND, OP_OR, OP_NOT};
@@ -380,13 +423,16 @@ int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, Seg *segs
     for (int oi = 0; oi < 7; ++oi) {
         const int op = order[oi];
         if (!(ops & bit[op])) continue;
+        const int first = n;
         if (op == OP_F || op == OP_G || op == OP_X || op == OP_NOT) {
             const uint64_t cnt = c->lvl_count[k - 1];
-            if (!cnt) continue;
-            Seg s{};
-            s.op = op; s.kind = SEG_UNARY; s.a_begin = c->lvl_begin[k - 1]; s.a_count = cnt;
-            s.n_tiles = (cnt + kTileU - 1) / kTileU;
-            add(s);
+            if (cnt) {
+                Seg s{};
+                s.op = op; s.kind = SEG_UNARY; s.a_begin = c->lvl_begin[k - 1]; s.a_count = cnt;
+                s.n_tiles = (cnt + kTileU - 1) / kTileU;
+                add(s);
+            }
+            close_group(op, first);
             continue;
         }
         for (int cl = 1; cl <= k - 2; ++cl) {
@@ -410,6 +456,7 @@ int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, Seg *segs
             }
             add(s);
         }
+        close_group(op, first);
     }
     return n;
 }
@@ -540,33 +587,41 @@ ltl_status run_learn(ltl_ctx *c, const uint32_t *d_letters_in, const uint64_t *d
     pb.groups = L.G;
     pb.spin_limit = c->opts.spin_limit ? c->opts.spin_limit : (1ull << 20);
 
-    const int blocks_per_sm = occupancy(c, L.Wt, L.C, L.NT);
-    const uint64_t max_grid = (uint64_t)blocks_per_sm * (uint64_t)c->n_sm;
+    int blocks_per_sm = 0;
+    if ((s = occupancy(c, L, OP_U, blocks_per_sm)) != LTL_OK) return s;
     memset(c->lvl_begin, 0, sizeof c->lvl_begin);
     memset(c->lvl_count, 0, sizeof c->lvl_count);
     uint64_t prev_entries = 0, prev_cands = 0;
     bool found = false;
     ltl_status result = LTL_NOT_FOUND;
+    OpGroup groups[8];
     for (int k = 1; k <= max_size; ++k) {
-        uint64_t total_tiles = 0;
-        const int n_segs = build_segments(c, k, ops, n_props, c->h_segs, total_tiles);
+        int n_groups = 0;
+        const int n_segs = build_segments(c, k, ops, n_props, c->h_segs, groups, n_groups);
         c->lvl_begin[k] = prev_entries;
-        if (n_segs == 0 || total_tiles == 0) {
+        if (n_segs == 0 || n_groups == 0) {
             // no candidate of this size (e.g. no connective allowed): the level is empty
             st.levels_done = k;
             continue;
         }
         CUDA_TRY(cudaMemcpyAsync(d_segs, c->h_segs, sizeof(Seg) * n_segs, cudaMemcpyHostToDevice, sm));
-        LevelArgs la{};
-        la.segs = d_segs;
-        la.n_segs = n_segs;
-        la.level = k;
-        la.total_tiles = total_tiles;
-        const int grid = (int)std::min<uint64_t>(total_tiles, max_grid);
         CUDA_TRY(cudaEventRecord(c->ev[2 * k], sm));
-        CUDA_TRY(launch_level(L.Wt, L.C, grid, L.NT, pb, la, sm));
+        for (int gi = 0; gi < n_groups; ++gi) {
+            const OpGroup &gr = groups[gi];
+            LevelArgs la{};
+            la.segs = d_segs + gr.first;
+            la.n_segs = gr.count;
+            la.level = k;
+            la.total_tiles = gr.tiles;
+            la.counter = k * 8 + gr.op;
+            int bps = 0;
+            if ((s = occupancy(c, L, gr.op, bps)) != LTL_OK) return s;
+            const int grid = (int)std::min<uint64_t>(gr.tiles, (uint64_t)bps * (uint64_t)c->n_sm);
+            void *args[] = {&pb, &la};
+            CUDA_TRY(cudaLaunchKernel(level_kernel_for(L, gr.op), dim3(grid), dim3(L.NT), args, L.smem, sm));
+            st.launches += 1;
+        }
         CUDA_TRY(cudaEventRecord(c->ev[2 * k + 1], sm));
-        st.launches += 1;
         CUDA_TRY(cudaMemcpyAsync(c->h_ctrl, d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, sm));
         CUDA_TRY(cudaStreamSynchronize(sm));
         st.d2h_bytes += sizeof(Ctrl);
@@ -594,6 +649,8 @@ ltl_status run_learn(ltl_ctx *c, const uint32_t *d_letters_in, const uint64_t *d
     st.n_traces = T;
     st.words_per_trace = (uint32_t)L.W;
     st.threads_per_cta = (uint32_t)L.NT;
+    st.batch = (uint32_t)L.NB;
+    st.ctas_per_sm = (uint32_t)blocks_per_sm;
     st.traces_per_thread = (uint32_t)(2 * L.C);
     st.chunk_groups = L.G;
     st.max_entries = L.max_entries;

@@ -1,0 +1,261 @@
+// ltl_level_common.cuh -- pieces shared by the size-level candidate kernels.
+//
+// A candidate (Section 3, handleOp) is one connective applied to cached
+// operands.  Its characteristic matrix (CM) is computed in registers, spread
+// over the CTA: thread `tid` owns, in chunk c of group g, the traces
+// t0 = 2 * ((g * C + c) * NT + tid) and t0 + 1, every bit-plane w of both.
+// The check-and-cache step then needs three CTA-wide facts: the NH
+// fingerprint (a sum, so the thread split does not matter), the soundness
+// test of eq. (dagger) (an AND over traces), and -- after a hash-set probe --
+// either a store of the new CM or a full compare with an equal-fingerprint
+// entry.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ltl_device.cuh"
+#include "ltl_types.h"
+
+namespace ltl {
+namespace lvl {
+
+__device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    return *(volatile const unsigned long long *)p;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int W, int C>
+struct Frag {
+    uint64_t v[C][2][W];   // [chunk][trace of the pair][word]
+};
+
+__host__ __device__ constexpr bool is_binary(int op) { return op == OP_AND || op == OP_OR || op == OP_U; }
+
+// Loads one thread's share of a CM: `base` points at plane 0, planes are
+// `plane` words apart, the thread's pair of chunk c starts at toff + c * cs.
+template <int W, int C, bool kReadOnly>
+__device__ __forceinline__ void load_frag(const uint64_t *base, uint64_t plane, uint64_t toff, uint64_t cs,
+                                          Frag<W, C> &f) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(base + (uint64_t)w * plane + toff + c * cs);
+            const ulonglong2 q = kReadOnly ? __ldg(p) : *p;
+            f.v[c][0][w] = q.x;
+            f.v[c][1][w] = q.y;
+        }
+    }
+}
+
+// The connective itself (Section 4): a = left operand (or the only one),
+// b = right operand; the result replaces r.  m is the length mask.
+template <int OP, int W, int C>
+__device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Frag<W, C> &m, int nsteps) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (OP == OP_ATOM) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
+            } else if (OP == OP_NOT) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) r.v[c][j][w] = m.v[c][j][w] & ~a.v[c][j][w];
+            } else if (OP == OP_X) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
+                op_x<W>(r.v[c][j]);
+            } else if (OP == OP_F) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
+                op_f<W>(r.v[c][j], nsteps);
+            } else if (OP == OP_G) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
+                op_g<W>(r.v[c][j], m.v[c][j], nsteps);
+            } else if (OP == OP_AND) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) r.v[c][j][w] &= a.v[c][j][w];
+            } else if (OP == OP_OR) {
+#pragma unroll
+                for (int w = 0; w < W; ++w) r.v[c][j][w] |= a.v[c][j][w];
+            } else if (OP == OP_U) {
+                op_u<W>(a.v[c][j], r.v[c][j], nsteps);   // r holds the right operand on entry
+            }
+        }
+    }
+}
+
+// Soundness bits of this thread's traces: bit (2c + j) = value at position 0.
+template <int W, int C>
+__device__ __forceinline__ uint32_t pos0_bits(const Frag<W, C> &r) {
+    uint32_t b = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) b |= ((uint32_t)r.v[c][j][0] & 1u) << (2 * c + j);
+    return b;
+}
+
+template <int W, int C>
+__device__ __forceinline__ void store_frag(const Frag<W, C> &r, uint64_t *dst, uint64_t plane, uint64_t toff,
+                                           uint64_t cs) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            ulonglong2 q;
+            q.x = r.v[c][0][w];
+            q.y = r.v[c][1][w];
+            *reinterpret_cast<ulonglong2 *>(dst + (uint64_t)w * plane + toff + c * cs) = q;
+        }
+    }
+}
+
+// Entries published during this launch are read through L2 only (ld.cg).
+template <int W, int C>
+__device__ __forceinline__ bool equal_frag(const Frag<W, C> &r, const uint64_t *src, uint64_t plane, uint64_t toff,
+                                           uint64_t cs) {
+    bool eq = true;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const ulonglong2 q =
+                __ldcg(reinterpret_cast<const ulonglong2 *>(src + (uint64_t)w * plane + toff + c * cs));
+            eq &= (q.x == r.v[c][0][w]) & (q.y == r.v[c][1][w]);
+        }
+    }
+    return eq;
+}
+
+template <int W, int C>
+__device__ __forceinline__ bool equal_regs(const Frag<W, C> &x, const Frag<W, C> &y) {
+    bool eq = true;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int w = 0; w < W; ++w) eq &= x.v[c][j][w] == y.v[c][j][w];
+    return eq;
+}
+
+enum : int { DEC_NEW = 0, DEC_CMP = 1, DEC_FAIL = 2, DEC_ERR = 3, DEC_DUP = 4, DEC_WAIT = 5 };
+
+// One probe run by a single thread from slot h: claims an empty slot
+// (DEC_NEW, with a freshly allocated entry index), or stops at a slot holding
+// the same fingerprint (DEC_CMP, with the entry to compare against).  If that
+// slot's entry is not yet published, the blocking form waits (bounded); the
+// non-blocking form returns DEC_WAIT with h left on the slot, for callers that
+// may hold unpublished claims of their own (waiting there could deadlock two
+// CTAs that each wait for the other's publication).
+template <bool kBlocking>
+__device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, unsigned long long &h,
+                                     unsigned long long &idx) {
+    for (unsigned long long n = 0; n <= pb.hmask; ++n) {
+        unsigned long long k = ld_volatile_u64(pb.hkeys + h);
+        if (k == 0ull) {
+            k = atomicCAS(pb.hkeys + h, 0ull, key);
+            if (k == 0ull) {
+                const unsigned long long i = atomicAdd(&pb.ctrl->n_entries, 1ull);
+                if (i >= pb.max_entries) {
+                    st_release_u32(pb.hvals + h, kValFail);
+                    atomicExch(&pb.ctrl->cap_hit, 1);
+                    return DEC_FAIL;
+                }
+                idx = i;
+                return DEC_NEW;
+            }
+        }
+        if (k == key) {
+            uint32_t v;
+            unsigned long long spins = 0;
+            while ((v = ld_acquire_u32(pb.hvals + h)) == kValPending) {
+                if (!kBlocking) return DEC_WAIT;
+                if (++spins > pb.spin_limit) {
+                    atomicAdd(&pb.ctrl->timeouts, 1ull);
+                    atomicCAS(&pb.ctrl->err, 0, -4 /* LTL_ERR_TIMEOUT */);
+                    atomicExch(&pb.ctrl->stop, 1);
+                    return DEC_ERR;
+                }
+                __nanosleep(64);
+            }
+            if (v == kValFail) return DEC_FAIL;
+            idx = v;
+            return DEC_CMP;
+        }
+        h = (h + 1) & pb.hmask;
+    }
+    atomicExch(&pb.ctrl->cap_hit, 1);   // table full
+    return DEC_FAIL;
+}
+
+__device__ __forceinline__ void record_separator(const Problem &pb, int level, uint64_t prov) {
+    if (atomicAdd(&pb.ctrl->found_count, 1u) == 0u) {
+        pb.ctrl->found_prov = prov;
+        pb.ctrl->found_level = level;
+    }
+    if (pb.stop_first) atomicExch(&pb.ctrl->stop, 1);
+}
+
+__device__ __forceinline__ unsigned long long fp_key(uint64_t s) {
+    const unsigned long long key = mix64(s);
+    return key ? key : 1ull;
+}
+
+// Decodes tile k of a segment into operand ranges [a0, a1) x [b0, b1).
+__device__ __forceinline__ void decode_tile(const Seg &sg, uint64_t k, uint64_t &a0, uint64_t &a1, uint64_t &b0,
+                                            uint64_t &b1) {
+    if (sg.kind == SEG_UNARY) {
+        a0 = k * kTileU;
+        a1 = min(a0 + kTileU, sg.a_count);
+        b0 = 0;
+        b1 = 1;
+        return;
+    }
+    uint64_t ta, tb;
+    if (sg.kind == SEG_RECT) {
+        if (sg.a_inner) { ta = k % sg.n_ta; tb = k / sg.n_ta; }
+        else { tb = k % sg.n_tb; ta = k / sg.n_tb; }
+    } else {
+        // upper-triangular tiles (ta <= tb), row-major: row ta holds n - ta tiles
+        const int64_t n = (int64_t)sg.n_ta;
+        const double dn = (double)n;
+        double est = ((2.0 * dn + 1.0) - sqrt((2.0 * dn + 1.0) * (2.0 * dn + 1.0) - 8.0 * (double)k)) * 0.5;
+        int64_t r = (int64_t)est;
+        if (r < 0) r = 0;
+        if (r > n - 1) r = n - 1;
+        auto row_start = [&](int64_t x) -> int64_t { return x * n - x * (x - 1) / 2; };
+        while (r > 0 && row_start(r) > (int64_t)k) --r;
+        while (r + 1 < n && row_start(r + 1) <= (int64_t)k) ++r;
+        ta = (uint64_t)r;
+        tb = ta + ((uint64_t)k - (uint64_t)row_start(r));
+    }
+    a0 = ta * kTileA;
+    a1 = min(a0 + kTileA, sg.a_count);
+    b0 = tb * kTileB;
+    b1 = min(b0 + kTileB, sg.b_count);
+}
+
+__device__ __forceinline__ int find_segment(const LevelArgs &la, unsigned long long tile) {
+    int si = 0;
+    while (si + 1 < la.n_segs && la.segs[si + 1].tile_begin <= tile) ++si;
+    return si;
+}
+
+}  // namespace lvl
+}  // namespace ltl

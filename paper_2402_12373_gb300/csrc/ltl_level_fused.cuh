@@ -1,0 +1,444 @@
+// ltl_level_fused.cuh -- the size-level candidate kernel for matrices that fit
+// in one CTA's registers (the common case: up to 4096 / W traces).
+//
+// Per size level one persistent launch; CTAs pull tiles (8 x 8 operand pairs,
+// or 16 operands for unary connectives) from a counter.  Within a tile a CTA
+// walks its candidates in batches of NB that share the left operand:
+//
+//   1. the batch's operand matrices arrive in shared memory by TMA bulk copies
+//      (cp.async.bulk, completion on an mbarrier), issued while the previous
+//      batch was in its hash phase;
+//   2. every thread computes its share of each candidate's matrix in
+//      registers (the connective by exponential propagation, Section 4), the
+//      NH fingerprint partial sums and the position-0 soundness bits;
+//   3. one CTA barrier reduces fingerprints and soundness over the CTA; a
+//      separator is recorded (eq. (dagger)); the next batch's copies are issued;
+//   4. lanes k < NB of warp 0 probe the device hash set in parallel, one
+//      candidate each; the CTA then stores new matrices (and a lane publishes
+//      the entry) or compares duplicates word by word with the stored entry.
+//
+// One kernel per connective (template OP): each launch of a level covers the
+// segments (splits) of one connective, so the compiler allocates registers
+// for that connective alone.
+#pragma once
+#include "ltl_level_common.cuh"
+
+namespace ltl {
+namespace lvl {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        "  .reg .pred p;\n"
+        "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "  selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// One-dimensional TMA bulk copy global -> shared, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// lane states of the hash phase (warp 0, one lane per candidate of the batch)
+enum : int { S_PROBE = 0, S_STORE = 1, S_CMP = 2, S_DONE = 3 };
+
+template <int NB>
+struct FusedShared {
+    unsigned long long fp[32][NB];
+    uint32_t bad[32];
+    unsigned long long tile;
+    unsigned long long idx[2][NB];
+    int dec[2][NB];
+    uint32_t neq[2];
+    alignas(8) uint64_t bar;
+};
+
+struct LaneConst {
+    uint64_t toff, cs, plane, stride;
+    uint32_t want, care;
+    int tid, lane, warp, nwarps;
+};
+
+// One thread's pair of traces (t0, t0 + 1) of one candidate: operands from
+// shared memory (pa: left / only operand, pb_: right operand of a binary
+// connective), the length mask from global memory (NOT and G only).
+template <int OP, int W>
+__device__ __forceinline__ void compute_pair(const uint64_t *pa, const uint64_t *pb_, const uint64_t *pm,
+                                             uint64_t plane, int nsteps, uint64_t (&out)[2][W]) {
+    constexpr bool BIN = is_binary(OP);
+    constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
+    uint64_t a[2][W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pa + (uint64_t)w * plane);
+        a[0][w] = q.x;
+        a[1][w] = q.y;
+    }
+    if (BIN) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb_ + (uint64_t)w * plane);
+            out[0][w] = q.x;
+            out[1][w] = q.y;
+        }
+    }
+    uint64_t m[2][W];
+    if (MASKED) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(pm + (uint64_t)w * plane));
+            m[0][w] = q.x;
+            m[1][w] = q.y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (OP == OP_ATOM) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
+        } else if (OP == OP_NOT) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[j][w] = m[j][w] & ~a[j][w];
+        } else if (OP == OP_X) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
+            op_x<W>(out[j]);
+        } else if (OP == OP_F) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
+            op_f<W>(out[j], nsteps);
+        } else if (OP == OP_G) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
+            op_g<W>(out[j], m[j], nsteps);
+        } else if (OP == OP_AND) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[j][w] &= a[j][w];
+        } else if (OP == OP_OR) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[j][w] |= a[j][w];
+        } else if (OP == OP_U) {
+            op_u<W>(a[j], out[j], nsteps);
+        }
+    }
+}
+
+template <int W, int C, int NB, int OP>
+__device__ __forceinline__ void fused_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0, uint64_t a1,
+                                           uint64_t b0, uint64_t b1, FusedShared<NB> &sh, uint64_t *slots,
+                                           uint32_t &phase, uint32_t &round, const LaneConst &lc,
+                                           unsigned long long &done) {
+    constexpr bool BIN = is_binary(OP);
+    const bool tri = sg.kind == SEG_TRI;
+    const uint64_t *srcA = (OP == OP_ATOM) ? pb.atoms : pb.arena;
+    const uint32_t cm_bytes = (uint32_t)(pb.stride * 8);
+    uint64_t ci = a0, cj = b0, loaded_a = ~0ull;
+
+    // next batch of the tile in (a outer, b inner) order; binary batches share a
+    auto next = [&](uint64_t &a, uint64_t &bf, int &nb) -> bool {
+        if constexpr (!BIN) {
+            if (ci >= a1) return false;
+            a = ci;
+            bf = 0;
+            nb = (int)min((uint64_t)NB, a1 - ci);
+            ci += (uint64_t)nb;
+            return true;
+        }
+        for (;;) {
+            if (ci >= a1) return false;
+            const uint64_t jb = tri ? max(b0, ci + 1) : b0;
+            if (cj < jb) cj = jb;
+            if (cj < b1) break;
+            ++ci;
+            cj = 0;
+        }
+        a = ci;
+        bf = cj;
+        nb = (int)min((uint64_t)NB, b1 - cj);
+        cj += (uint64_t)nb;
+        return true;
+    };
+    // thread 0 issues the TMA copies of a batch (all threads track loaded_a)
+    auto issue = [&](uint64_t a, uint64_t bf, int nb) {
+        const bool reload_a = BIN && (a != loaded_a);
+        if (lc.tid == 0) {
+            const uint32_t n = (uint32_t)nb + (reload_a ? 1u : 0u);
+            mbar_arrive_expect_tx(&sh.bar, n * cm_bytes);
+            if (BIN) {
+                if (reload_a) bulk_g2s(slots + (uint64_t)NB * lc.stride, srcA + (sg.a_begin + a) * pb.stride, cm_bytes, &sh.bar);
+                for (int k = 0; k < nb; ++k)
+                    bulk_g2s(slots + (uint64_t)k * lc.stride, pb.arena + (sg.b_begin + bf + k) * pb.stride, cm_bytes,
+                             &sh.bar);
+            } else {
+                for (int k = 0; k < nb; ++k)
+                    bulk_g2s(slots + (uint64_t)k * lc.stride, srcA + (sg.a_begin + a + k) * pb.stride, cm_bytes,
+                             &sh.bar);
+            }
+        }
+        if (BIN) loaded_a = a;
+    };
+    auto wait_data = [&]() {
+        unsigned long long spins = 0;
+        while (!mbar_try_wait(&sh.bar, phase)) {
+            if (++spins > pb.spin_limit) {
+                atomicCAS(&pb.ctrl->err, 0, -4 /* LTL_ERR_TIMEOUT */);
+                atomicExch(&pb.ctrl->stop, 1);
+                break;
+            }
+        }
+        phase ^= 1u;
+    };
+
+    uint64_t a, bf;
+    int nb;
+    bool have = next(a, bf, nb);
+    if (have) issue(a, bf, nb);
+    while (have) {
+        wait_data();
+        // ---- 2. candidates of the batch in registers
+        Frag<W, C> r[NB];
+        uint64_t fp[NB];
+        uint32_t badm = 0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            fp[k] = 0;
+            if (k < nb) {
+                const uint64_t *sa = slots + (uint64_t)(BIN ? NB : k) * lc.stride + lc.toff;
+                const uint64_t *sb = slots + (uint64_t)k * lc.stride + lc.toff;
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    compute_pair<OP, W>(sa + c * lc.cs, sb + c * lc.cs, pb.mask + lc.toff + c * lc.cs, lc.plane,
+                                        pb.nsteps, r[k].v[c]);
+                const uint32_t bits = pos0_bits<W, C>(r[k]);
+                badm |= (((bits ^ lc.want) & lc.care) != 0u ? 1u : 0u) << k;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const ulonglong2 key =
+                    __ldg(reinterpret_cast<const ulonglong2 *>(pb.keys + (uint64_t)w * lc.plane + lc.toff + c * lc.cs));
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    if (k < nb) fp[k] += nh_term(r[k].v[c][0][w], key.x) + nh_term(r[k].v[c][1][w], key.y);
+            }
+        }
+        // ---- 3. CTA reduction (also frees the operand slots)
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], off);
+        badm = __reduce_or_sync(0xffffffffu, badm);
+        if (lc.lane == 0) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) sh.fp[lc.warp][k] = fp[k];
+            sh.bad[lc.warp] = badm;
+        }
+        __syncthreads();
+        const uint64_t cur_a = a, cur_bf = bf;
+        const int cur_nb = nb;
+        have = next(a, bf, nb);
+        if (have) issue(a, bf, nb);
+
+        // ---- 4. hash phase: warp 0 lane k owns candidate k
+        int state = S_DONE;
+        unsigned long long key = 0, h = 0, idx = 0, waits = 0;
+        uint64_t prov = 0;
+        if (lc.warp == 0 && lc.lane < cur_nb) {
+            uint64_t s = 0;
+            uint32_t bad = 0;
+            for (int w2 = 0; w2 < lc.nwarps; ++w2) {
+                s += sh.fp[w2][lc.lane];
+                bad |= sh.bad[w2];
+            }
+            if (BIN) prov = prov_pack(OP, sg.a_begin + cur_a, sg.b_begin + cur_bf + lc.lane);
+            else prov = prov_pack(OP, sg.a_begin + cur_a + lc.lane, 0);
+            if (!((bad >> lc.lane) & 1u)) record_separator(pb, level, prov);
+            key = fp_key(s);
+            h = key & pb.hmask;
+            state = S_PROBE;
+        }
+        for (;;) {
+            const int slot = (int)(round & 1u);
+            if (lc.warp == 0) {
+                // a candidate waits while an earlier one of the batch with the
+                // same fingerprint is unsettled (it may be its pending entry)
+                bool blocked = false;
+#pragma unroll
+                for (int k2 = 0; k2 < NB; ++k2) {
+                    const unsigned long long key2 = __shfl_sync(0xffffffffu, key, k2);
+                    const int st2 = __shfl_sync(0xffffffffu, state, k2);
+                    if (k2 < lc.lane && st2 != S_DONE && key2 == key) blocked = true;
+                }
+                int dec = DEC_DUP;
+                if (state == S_PROBE) {
+                    if (!blocked) dec = probe<false>(pb, key, h, idx);
+                    if (blocked || dec == DEC_WAIT) {
+                        // retried next round, after every CTA has published the
+                        // claims of its current round (bounded by spin_limit)
+                        dec = DEC_WAIT;
+                        if (++waits > pb.spin_limit) {
+                            atomicAdd(&pb.ctrl->timeouts, 1ull);
+                            atomicCAS(&pb.ctrl->err, 0, -4 /* LTL_ERR_TIMEOUT */);
+                            atomicExch(&pb.ctrl->stop, 1);
+                            dec = DEC_ERR;
+                            state = S_DONE;
+                        } else if (!blocked) {
+                            __nanosleep(128);
+                        }
+                    } else {
+                        state = dec == DEC_NEW ? S_STORE : dec == DEC_CMP ? S_CMP : S_DONE;
+                    }
+                }
+                if (lc.lane < NB) {
+                    sh.dec[slot][lc.lane] = (lc.lane < cur_nb) ? dec : DEC_DUP;
+                    sh.idx[slot][lc.lane] = idx;
+                }
+            }
+            __syncthreads();   // A: decisions visible
+            if (lc.tid == 0) sh.neq[slot ^ 1] = 0u;
+            uint32_t neq = 0;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int d = sh.dec[slot][k];
+                if (d == DEC_NEW) {
+                    store_frag<W, C>(r[k], pb.arena + sh.idx[slot][k] * pb.stride, lc.plane, lc.toff, lc.cs);
+                } else if (d == DEC_CMP) {
+                    if (!equal_frag<W, C>(r[k], pb.arena + sh.idx[slot][k] * pb.stride, lc.plane, lc.toff, lc.cs))
+                        neq |= 1u << k;
+                }
+            }
+            neq = __reduce_or_sync(0xffffffffu, neq);
+            if (lc.lane == 0 && neq) atomicOr(&sh.neq[slot], neq);
+            __syncthreads();   // B: stores issued, compare verdicts in
+            const uint32_t nq = sh.neq[slot];
+            bool more = false;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int d = sh.dec[slot][k];
+                more |= (d == DEC_WAIT) || (d == DEC_CMP && ((nq >> k) & 1u));
+            }
+            if (lc.warp == 0) {
+                if (state == S_STORE) {
+                    pb.prov[idx] = prov;
+                    __threadfence();
+                    st_release_u32(pb.hvals + h, (uint32_t)idx);
+                    state = S_DONE;
+                } else if (state == S_CMP) {
+                    if ((nq >> lc.lane) & 1u) {   // same fingerprint, different matrix
+                        atomicAdd(&pb.ctrl->collisions, 1ull);
+                        h = (h + 1) & pb.hmask;
+                        state = S_PROBE;
+                    } else {
+                        state = S_DONE;
+                    }
+                    atomicAdd(&pb.ctrl->compares, 1ull);
+                }
+                __syncwarp();
+            }
+            ++round;
+            if (!more) break;
+        }
+        done += (unsigned long long)cur_nb;
+    }
+}
+
+}  // namespace
+
+template <int W, int C, int NB, int OP>
+__global__ void __launch_bounds__(256, 2) fused_level_kernel(Problem pb, LevelArgs la) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    uint64_t *slots = reinterpret_cast<uint64_t *>(dyn_smem);
+    __shared__ FusedShared<NB> sh;
+    LaneConst lc;
+    lc.tid = threadIdx.x;
+    lc.lane = lc.tid & 31;
+    lc.warp = lc.tid >> 5;
+    lc.nwarps = blockDim.x >> 5;
+    lc.toff = 2ull * (uint64_t)lc.tid;
+    lc.cs = 2ull * (uint64_t)blockDim.x;
+    lc.plane = pb.plane;
+    lc.stride = pb.stride;
+    lc.want = 0;
+    lc.care = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const uint64_t t = lc.toff + c * lc.cs + j;
+            if (t < pb.n_pos) lc.want |= 1u << (2 * c + j);
+            if (t < pb.n_traces) lc.care |= 1u << (2 * c + j);
+        }
+    if (lc.tid == 0) {
+        mbar_init(&sh.bar, 1);
+        sh.neq[0] = sh.neq[1] = 0u;
+    }
+    __syncthreads();
+    uint32_t phase = 0, round = 0;
+    unsigned long long done = 0;
+    for (;;) {
+        if (lc.tid == 0) {
+            unsigned long long t = ~0ull;
+            if (!ld_volatile_i32(&pb.ctrl->stop)) t = atomicAdd(&pb.ctrl->next_tile[la.counter], 1ull);
+            sh.tile = t;
+        }
+        __syncthreads();
+        const unsigned long long tile = sh.tile;
+        __syncthreads();
+        if (tile >= la.total_tiles) break;
+        const Seg sg = la.segs[find_segment(la, tile)];
+        uint64_t a0, a1, b0, b1;
+        decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
+        fused_tile<W, C, NB, OP>(pb, la.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done);
+    }
+    if (lc.tid == 0 && done) atomicAdd(&pb.ctrl->cands, done);
+}
+
+}  // namespace lvl
+
+// candidates per batch: 2 when a thread holds 8 words per candidate, else 4
+template <int W, int C>
+struct FusedNB {
+    static constexpr int value = (W * C >= 8) ? 2 : 4;
+};
+
+template <int W, int C>
+const void *fused_fn(int op) {
+    constexpr int NB = FusedNB<W, C>::value;
+    switch (op) {
+    case OP_ATOM: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_ATOM>);
+    case OP_NOT: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_NOT>);
+    case OP_AND: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_AND>);
+    case OP_OR: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_OR>);
+    case OP_X: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_X>);
+    case OP_F: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_F>);
+    case OP_G: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_G>);
+    case OP_U: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_U>);
+    default: return nullptr;
+    }
+}
+
+}  // namespace ltl

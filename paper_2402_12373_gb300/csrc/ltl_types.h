@@ -50,7 +50,7 @@ struct Ctrl {
     unsigned long long cands;          // candidates processed (cumulative)
     unsigned long long compares;       // full-matrix compares after fingerprint match
     unsigned long long collisions;     // compares that found a different matrix
-    unsigned long long next_tile[kMaxLevels];
+    unsigned long long next_tile[kMaxLevels * 8];   // per (size level, connective)
     unsigned int found_count;          // separators seen (first one is recorded)
     int stop;                          // 1: CTAs leave at the next tile boundary
     int cap_hit;
@@ -84,11 +84,14 @@ struct Problem {
     unsigned long long spin_limit;
 };
 
+// One launch: the segments of one connective at one size level.
 struct LevelArgs {
     const Seg *segs;
     int32_t n_segs;
     int32_t level;
     uint64_t total_tiles;
+    int32_t counter;       // tile counter slot: level * 8 + connective
+    int32_t pad;
 };
 
 }  // namespace ltl
