@@ -185,6 +185,43 @@ ltl_status ltl_ctx_level_range(ltl_ctx *ctx, int level, uint64_t *begin, uint64_
 ltl_status ltl_ctx_entry(ltl_ctx *ctx, uint64_t idx, char *formula_out, size_t formula_cap,
                          uint64_t *cs_out, int words_per_trace);
 
+/* ---------------------------------------------------------------------------
+ * ltl_eval_noalloc -- ltl_eval for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment variant of ltl_eval.
+ *
+ * Who needs it: code that runs where allocation is not allowed -- inside a
+ * framework that owns all device memory through its own pool, in a real-time
+ * loop that must not allocate after start-up, or where the implicit
+ * synchronisation of cudaMalloc / cudaFree is unacceptable.  This call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *
+ *   formula          text as for ltl_eval; atoms must be < n_props.
+ *   d_letters,       the traces, already in DEVICE memory (layout as in
+ *   d_offsets        ltl_traces); read only.
+ *   n_traces         number of traces.
+ *   max_len          >= the longest trace (<= 1024).
+ *   d_cs_out         DEVICE buffer of n_traces * words_per_trace uint64, trace
+ *                    major as for ltl_eval, written by the call.
+ *   words_per_trace  >= ceil(max_len / 64).
+ *   stream           cudaStream_t the work runs on (NULL: legacy default
+ *                    stream); the call returns after the stream has finished it.
+ *
+ * Scratch: one file-scope static device array of LTL_NOALLOC_SCRATCH_BYTES
+ * (64 MiB), held by every GPU that loads the library until the process exits.
+ * A call needing more (about 8 * (1 + n_props + stack depth) * ceil(max_len/64)
+ * * n_traces bytes) is rejected with LTL_ERR_OOM and a message giving the
+ * size.  All calls on a device share the array and it keeps the last call's
+ * contents; each call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU (other streams or host threads) race on the array: the
+ * caller must serialise them.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.
+ * -------------------------------------------------------------------------*/
+#define LTL_NOALLOC_SCRATCH_BYTES (64ull << 20)
+ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_letters, const uint64_t *d_offsets,
+                            uint64_t n_traces, uint32_t max_len, int n_props, uint64_t *d_cs_out,
+                            int words_per_trace, void *stream);
+
 /* Message of the last error on this host thread (static storage). */
 const char *ltl_last_error(void);
 

@@ -27,7 +27,7 @@ MAX_LEVELS = 64
 # Every symbol include/ltl.h declares.
 EXPORTS = ["ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_destroy", "ltl_ctx_learn",
            "ltl_ctx_learn_device", "ltl_ctx_level_range", "ltl_ctx_entry", "ltl_last_error",
-           "ltl_version"]
+           "ltl_version", "ltl_eval_noalloc"]
 
 
 class LtlError(RuntimeError):
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True):
                                        ctypes.c_size_t, ctypes.POINTER(Stats)]
     L.ltl_ctx_level_range.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(u64)]
     L.ltl_ctx_entry.argtypes = [vp, u64, ctypes.c_char_p, ctypes.c_size_t, vp, i32]
+    L.ltl_eval_noalloc.argtypes = [ctypes.c_char_p, vp, vp, u64, u32, i32, vp, i32, vp]
+    L.ltl_eval_noalloc.restype = ctypes.c_int
     L.ltl_last_error.restype = ctypes.c_char_p
     L.ltl_version.restype = ctypes.c_char_p
     for f in ("ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_learn", "ltl_ctx_learn_device",
@@ -272,6 +274,19 @@ def evaluate(formula: str, traces, n_props: int, words_per_trace: Optional[int] 
     rc = L.ltl_eval(formula.encode(), ctypes.byref(ht.struct), n_props, out.ctypes.data, words_per_trace)
     _check(rc, ok=(LTL_OK,))
     return out[:n]
+
+
+def evaluate_noalloc(formula: str, letters, offsets, n_traces: int, max_len: int, n_props: int, out,
+                     words_per_trace: int, stream=None) -> None:
+    """ltl_eval_noalloc on device tensors (letters int32/uint32, offsets int64,
+    out int64 [n_traces, words_per_trace]); allocates no device memory."""
+    L = load()
+    if stream is None:
+        stream = _current_stream()
+    rc = L.ltl_eval_noalloc(formula.encode(), ctypes.c_void_p(letters.data_ptr()),
+                            ctypes.c_void_p(offsets.data_ptr()), n_traces, max_len, n_props,
+                            ctypes.c_void_p(out.data_ptr()), words_per_trace, stream)
+    _check(rc, ok=(LTL_OK,))
 
 
 def version() -> str:

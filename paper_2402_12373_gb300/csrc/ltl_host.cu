@@ -907,3 +907,12 @@ ltl_status ltl_eval(const char *formula, const ltl_traces *traces, int n_props, 
 }
 
 }  // extern "C"
+
+// Entry points for other translation units of the library.
+namespace ltl {
+bool compile_formula_program(const char *text, int n_props, std::vector<uint32_t> &prog, int &depth) {
+    int max_atom = -1;
+    return compile_formula(text, n_props, prog, depth, max_atom);
+}
+ltl_status set_error(ltl_status s, const char *msg) { return fail(s, "%s", msg); }
+}  // namespace ltl

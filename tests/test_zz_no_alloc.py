@@ -1,0 +1,62 @@
+"""ltl_eval_noalloc: formula evaluation for callers that cannot allocate device
+memory (a framework that owns the whole device through its own pool, a
+real-time loop that must not allocate after start-up, code that cannot afford
+the synchronisation of cudaMalloc / cudaFree).  The call takes device-resident
+traces, writes a device-resident result and keeps its scratch in one static
+device array of LTL_NOALLOC_SCRATCH_BYTES.
+
+Its result must equal that of ltl_eval (the allocating entry point) bit for
+bit, on two calls in a row -- the second one smaller than the first, so stale
+scratch contents from the first call would show up if a part that must start
+at zero were not cleared.  This file is collected last on purpose.
+"""
+import ctypes
+import random
+
+import numpy as np
+import pytest
+
+from paper_2402_12373_gb300 import _lib as L
+from paper_2402_12373_gb300 import synth
+
+
+def _rand_traces(seed, n, n_props, lo, hi):
+    rng = random.Random(seed)
+    return synth.TraceSet.from_list(
+        [[rng.randrange(1 << n_props) for _ in range(rng.randrange(lo, hi + 1))] for _ in range(n)])
+
+
+@pytest.mark.gpu
+def test_noalloc_matches_ltl_eval_on_two_calls_in_a_row():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    cases = [
+        # larger first: three words per trace, U / G / X nesting
+        ("((p0 U (p1 & X p2)) | G !p3)", _rand_traces(1, 3000, 4, 100, 190), 4),
+        # then smaller: the plain-single traces
+        ("F (p0 & X p1)", synth.plain_single().P, 2),
+    ]
+    for formula, ts, n_props in cases:
+        n = ts.n
+        max_len = int(ts.lengths().max())
+        W = (max_len + 63) // 64
+        want = L.evaluate(formula, ts, n_props, words_per_trace=W)          # allocating entry point
+        d_letters = torch.from_numpy(ts.letters.astype(np.int32)).cuda()
+        d_offsets = torch.from_numpy(ts.offsets.astype(np.int64)).cuda()
+        d_out = torch.full((n, W), -1, dtype=torch.int64, device="cuda")   # poisoned output
+        L.evaluate_noalloc(formula, d_letters, d_offsets, n, max_len, n_props, d_out, W)
+        torch.cuda.synchronize()
+        got = d_out.cpu().numpy().view(np.uint64)
+        assert got.shape == want.shape
+        assert np.array_equal(got, want), formula
+
+
+def test_noalloc_rejects_work_beyond_the_static_scratch():
+    """A size beyond LTL_NOALLOC_SCRATCH_BYTES is refused before any device work."""
+    lib = L.load()
+    n = 1 << 20                                    # 1M traces x 16 words x (1 + 2 + 2) CMs > 64 MiB
+    fake = ctypes.c_void_p(256)                     # never dereferenced: rejected on the host
+    rc = lib.ltl_eval_noalloc(b"(p0 U p1)", fake, fake, n, 1024, 2, fake, 16, None)
+    assert rc == L.LTL_ERR_OOM
+    msg = L.last_error()
+    assert "static scratch" in msg and "bytes" in msg
