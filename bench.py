@@ -54,17 +54,19 @@ def units_of(stats, T):
     return sum(stats["candidates"][k] for k in range(1, d + 1)) * T
 
 
-def level_bytes(stats, k, T, W, n_props):
-    """Algorithmic HBM bytes of level k's launch: every candidate reads its
+def level_bytes(stats, k, T, n_props):
+    """Algorithmic HBM bytes of level k's launches: every candidate reads its
     operand matrices and either writes its matrix (new) or reads one for the
-    full compare (duplicate): (operands + 1) * 8 * W bytes per trace."""
+    full compare (duplicate): (operands + 1) * (bytes per trace) per trace,
+    8 * W bytes per trace (4 in the narrow layout, two traces per word)."""
     cand = stats["candidates"][k]
     if k == 1:
         unary, binary = cand, 0
     else:
         unary = min(cand, N_UNARY * stats["unique"][k - 1])
         binary = cand - unary
-    return (unary * 2 + binary * 3) * T * W * 8
+    per_trace = 4 if stats["traces_per_word"] == 2 else 8 * stats["words_per_trace"]
+    return (unary * 2 + binary * 3) * T * per_trace
 
 
 def kernel_sources_sha():
@@ -209,6 +211,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-size", type=int, default=MAX_SIZE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-chunks", type=int, default=0,
+                    help="launch-shape cap (16-byte chunks per thread); 0 = automatic")
     ap.add_argument("--ws-gb", type=float, default=0.0,
                     help="workspace size in GB (default: half of the free device memory)")
     args = ap.parse_args()
@@ -241,7 +245,7 @@ def main():
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = L.Context(workspace=ws, stop=L.STOP_NONE)
+    ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks)
 
     def step():
         return ctx.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
@@ -288,7 +292,7 @@ def main():
     # dominant kernel: the level launch with the longest device time
     kd = max(range(1, r0["levels_done"] + 1), key=lambda k: sum(r["ms"][k] for r in results))
     kd_ms = statistics.mean(r["ms"][kd] for r in results)
-    kd_bytes = level_bytes(r0, kd, T, W, spec.n_props)
+    kd_bytes = level_bytes(r0, kd, T, spec.n_props)
     peaks, peak_src = measured_peaks()
     achieved = kd_bytes / (kd_ms / 1e3) / 1e9
     sha = kernel_sources_sha()
@@ -333,6 +337,8 @@ def main():
                        "parallelism": "independent problem per rank (seed = rank)" if world > 1 else "1 GPU",
                        "launch": {"threads_per_cta": r0["threads_per_cta"],
                                   "traces_per_thread": r0["traces_per_thread"],
+                                  "traces_per_word": r0["traces_per_word"],
+                                  "batch": r0["batch"], "ctas_per_sm": r0["ctas_per_sm"],
                                   "chunk_groups": r0["chunk_groups"]}},
             "levels": {"unique": r0["unique"][1:], "candidates": r0["candidates"][1:],
                        "ms": [round(x, 4) for x in r0["ms"][1:]], "entries": r0["entries"]},

@@ -90,6 +90,9 @@ typedef struct {
                                     for all device state (>= 256-byte aligned) */
     uint64_t workspace_bytes;
     const char *autotune_path;   /* reserved, may be NULL                     */
+    uint32_t max_chunks;         /* launch-shape cap: at most this many 16-byte
+                                    chunks per thread (rounded up to a power of
+                                    two); 0 = automatic                        */
 } ltl_opts;
 
 #define LTL_MAX_LEVELS 64
@@ -109,6 +112,7 @@ typedef struct {
     uint32_t traces_per_thread;
     uint32_t chunk_groups;                /* 1: candidates kept in registers   */
     uint32_t batch;                       /* candidates per CTA batch          */
+    uint32_t traces_per_word;             /* 2: narrow layout (traces <= 32)   */
     uint32_t ctas_per_sm;                 /* resident CTAs per SM              */
     uint64_t launches;                    /* kernels launched by the call       */
     uint64_t h2d_bytes, d2h_bytes;        /* host<->device bytes copied         */

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("stop_on_solution", ctypes.c_int),
                 ("spin_limit", ctypes.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("user", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_uint64), ("autotune_path", ctypes.c_char_p)]
+                ("workspace_bytes", ctypes.c_uint64), ("autotune_path", ctypes.c_char_p),
+                ("max_chunks", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -58,6 +59,7 @@ class Stats(ctypes.Structure):
                 ("n_traces", ctypes.c_uint64), ("words_per_trace", ctypes.c_uint32),
                 ("threads_per_cta", ctypes.c_uint32), ("traces_per_thread", ctypes.c_uint32),
                 ("chunk_groups", ctypes.c_uint32), ("batch", ctypes.c_uint32),
+                ("traces_per_word", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("launches", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
@@ -73,6 +75,7 @@ class Stats(ctypes.Structure):
             "words_per_trace": int(self.words_per_trace), "threads_per_cta": int(self.threads_per_cta),
             "traces_per_thread": int(self.traces_per_thread), "chunk_groups": int(self.chunk_groups),
             "batch": int(self.batch), "ctas_per_sm": int(self.ctas_per_sm),
+            "traces_per_word": int(self.traces_per_word),
             "launches": int(self.launches), "h2d_bytes": int(self.h2d_bytes),
             "d2h_bytes": int(self.d2h_bytes), "max_entries": int(self.max_entries),
             "total_ms": float(self.total_ms),
@@ -144,7 +147,7 @@ class _HostTraces:
 
 
 def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int = 0,
-          spin_limit: int = 0) -> Opts:
+          spin_limit: int = 0, max_chunks: int = 0) -> Opts:
     o = Opts()
     o.mem_budget_bytes = int(mem_budget)
     o.stop_on_solution = int(stop)
@@ -156,6 +159,7 @@ def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int =
     o.workspace = None
     o.workspace_bytes = 0
     o.autotune_path = None
+    o.max_chunks = int(max_chunks)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -180,14 +184,14 @@ class Context:
     """A reusable learner context: stream + torch workspace + last cache."""
 
     def __init__(self, workspace=None, stop: int = STOP_FIRST, stream=None, mem_budget: int = 0,
-                 spin_limit: int = 0, workspace_bytes: Optional[int] = None):
+                 spin_limit: int = 0, workspace_bytes: Optional[int] = None, max_chunks: int = 0):
         self._L = load()
         if workspace is None:
             workspace = default_workspace(workspace_bytes)
         self.workspace = workspace
         if stream is None:
             stream = _current_stream()
-        self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit)
+        self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit, max_chunks)
         h = ctypes.c_void_p()
         _check(self._L.ltl_ctx_create(ctypes.byref(self._opts), ctypes.byref(h)), ok=(LTL_OK,))
         self._h = h

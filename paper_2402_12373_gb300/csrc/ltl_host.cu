@@ -24,11 +24,15 @@ namespace ltl {
 const void *fused_kernel_ptr_w1(int C, int op);
 const void *fused_kernel_ptr_w2(int C, int op);
 const void *fused_kernel_ptr_w48(int W, int C, int op);
+const void *fused_kernel_ptr_narrow(int C, int op);
+cudaError_t launch_pack_narrow(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
+                               int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
+                               cudaStream_t s);
 const void *stream_kernel_ptr(int W, int C);
 inline const void *fused_kernel_ptr(int W, int C, int op) {
     return W == 1 ? fused_kernel_ptr_w1(C, op) : W == 2 ? fused_kernel_ptr_w2(C, op) : fused_kernel_ptr_w48(W, C, op);
 }
-inline int fused_batch(int W, int C) { return (W * C >= 8) ? 2 : 4; }
+int fused_kernel_batch(int W, int C, bool narrow);
 cudaError_t launch_pack(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
                         int W, int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
                         cudaStream_t s);
@@ -211,6 +215,7 @@ size_t tokens_to_text(const uint32_t *tok, int n, int i, std::string &out) {
 
 struct Layout {
     int W = 0, Wt = 0, C = 0, NT = 0, NB = 1;
+    bool narrow = false;   // two traces of <= 32 positions per word
     size_t smem = 0;
     uint32_t G = 0;
     uint32_t n_traces = 0, n_pos = 0;
@@ -296,21 +301,37 @@ ltl_status plan(ltl_ctx *c, uint64_t n_pos, uint64_t n_neg, uint64_t max_len, ui
     const int Cmax = 8 / L.Wt;
     const uint64_t maxNT = 256;
     const uint64_t pairs = std::max<uint64_t>(1, (T + 1) / 2);
-    if (pairs <= maxNT * (uint64_t)Cmax) {
-        uint64_t nt = pow2_ceil((pairs + Cmax - 1) / Cmax);
+    // narrow layout: every trace fits 32 bits and the matrix fits one CTA;
+    // a thread then holds C words of two traces each per 16-byte chunk pair
+    const uint64_t quads = std::max<uint64_t>(1, (T + 3) / 4);
+    const uint64_t cap_c = c->opts.max_chunks ? pow2_ceil(c->opts.max_chunks) : 8;
+    const uint64_t ncmax = std::min<uint64_t>(4, cap_c);
+    // the smallest power-of-two thread count >= 32 that holds `units` with at
+    // most `cmax` chunks per thread, and the chunk count it then needs
+    auto shape = [&](uint64_t units, uint64_t cmax) {
+        uint64_t nt = pow2_ceil((units + cmax - 1) / cmax);
         nt = std::min<uint64_t>(std::max<uint64_t>(nt, 32), maxNT);
-        uint64_t cc = pow2_ceil((pairs + nt - 1) / nt);
         L.NT = (int)nt;
-        L.C = (int)std::min<uint64_t>(cc, (uint64_t)Cmax);
+        L.C = (int)std::min<uint64_t>(pow2_ceil((units + nt - 1) / nt), cmax);
         L.G = 1;
-        L.NB = fused_batch(L.Wt, L.C);
+    };
+    if (max_len <= 32 && quads <= maxNT * ncmax) {
+        shape(quads, ncmax);                       // narrow, fused
+        L.narrow = true;
+    } else if (pairs <= maxNT * std::min<uint64_t>(Cmax, cap_c)) {
+        shape(pairs, std::min<uint64_t>(Cmax, cap_c));   // wide, fused, capped shape
+    } else if (pairs <= maxNT * (uint64_t)Cmax) {
+        shape(pairs, (uint64_t)Cmax);              // wide, fused (the cap cannot hold the matrix)
     } else {
-        L.NT = (int)maxNT;
+        L.NT = (int)maxNT;                         // wide, two-pass streaming, >= 2 groups
         L.C = Cmax;
         L.G = (uint32_t)((pairs + maxNT * Cmax - 1) / (maxNT * Cmax));
-        L.NB = 1;
     }
-    L.plane = (uint64_t)L.G * L.C * 2 * L.NT;
+    // the batch size the fused kernel of this shape was compiled with (the
+    // shared-memory operand slots are sized from it)
+    L.NB = L.G == 1 ? fused_kernel_batch(L.Wt, L.C, L.narrow) : 1;
+    if (L.G == 1 && L.NB < 1) return fail(LTL_ERR_INVALID, "no fused kernel for W=%d C=%d", L.Wt, L.C);
+    L.plane = (uint64_t)L.G * L.C * 2 * L.NT;   // words per bit-plane
     L.stride = (uint64_t)L.Wt * L.plane;
     L.smem = L.G == 1 ? (size_t)(L.NB + 1) * 8 * L.stride : 0;
 
@@ -366,6 +387,7 @@ ltl_status plan(ltl_ctx *c, uint64_t n_pos, uint64_t n_neg, uint64_t max_len, ui
 }
 
 const void *level_kernel_for(const Layout &L, int op) {
+    if (L.narrow) return fused_kernel_ptr_narrow(L.C, op);
     return L.G == 1 ? fused_kernel_ptr(L.Wt, L.C, op) : stream_kernel_ptr(L.Wt, L.C);
 }
 
@@ -397,24 +419,64 @@ struct OpGroup {
     uint64_t tiles;
 };
 
-int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, Seg *segs, OpGroup *groups, int &n_groups) {
+// Tile extents for a launch of `cands` candidates on `slots` resident CTAs:
+// about four tiles per CTA, never fewer than `nb` candidates per tile.
+uint32_t tile_target(uint64_t cands, uint64_t slots, int nb) {
+    uint64_t cpt = cands / std::max<uint64_t>(1, 4 * slots);
+    cpt = std::max<uint64_t>(cpt, (uint64_t)nb);
+    return (uint32_t)std::min<uint64_t>(pow2_ceil(cpt), (uint64_t)kTileA * kTileB);
+}
+
+void set_tiles(Seg &s, uint32_t cpt) {
+    if (s.kind == SEG_UNARY) {
+        s.ta = std::min<uint32_t>(cpt, kTileU);
+        s.tb = 1;
+        s.n_tiles = (s.a_count + s.ta - 1) / s.ta;
+        return;
+    }
+    if (s.kind == SEG_TRI) {
+        uint32_t side = 2;
+        while (side < kTileA && side * side < cpt) side *= 2;
+        s.ta = s.tb = side;
+        s.n_ta = s.n_tb = (uint32_t)((s.a_count + side - 1) / side);
+        s.n_tiles = (uint64_t)s.n_ta * (s.n_ta + 1) / 2;
+        return;
+    }
+    s.tb = std::min<uint32_t>(cpt, kTileB);
+    s.ta = std::max<uint32_t>(1, std::min<uint32_t>(cpt / s.tb, kTileA));
+    s.n_ta = (uint32_t)((s.a_count + s.ta - 1) / s.ta);
+    s.n_tb = (uint32_t)((s.b_count + s.tb - 1) / s.tb);
+    s.n_tiles = (uint64_t)s.n_ta * s.n_tb;
+    s.a_inner = s.n_ta <= s.n_tb ? 1 : 0;
+}
+
+uint64_t seg_candidates(const Seg &s) {
+    if (s.kind == SEG_UNARY) return s.a_count;
+    if (s.kind == SEG_TRI) return s.a_count * (s.a_count - 1) / 2;
+    return s.a_count * s.b_count;
+}
+
+int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, uint64_t slots, int nb, Seg *segs,
+                   OpGroup *groups, int &n_groups) {
     int n = 0;
     n_groups = 0;
-    uint64_t total = 0;
-    auto add = [&](Seg s) {
-        s.tile_begin = total;
-        total += s.n_tiles;
-        segs[n++] = s;
-    };
     auto close_group = [&](int op, int first) {
-        if (n > first) groups[n_groups++] = OpGroup{op, first, n - first, total};
-        total = 0;
+        if (n <= first) return;
+        uint64_t cands = 0;
+        for (int i = first; i < n; ++i) cands += seg_candidates(segs[i]);
+        const uint32_t cpt = tile_target(cands, slots, nb);
+        uint64_t total = 0;
+        for (int i = first; i < n; ++i) {
+            set_tiles(segs[i], cpt);
+            segs[i].tile_begin = total;
+            total += segs[i].n_tiles;
+        }
+        groups[n_groups++] = OpGroup{op, first, n - first, total};
     };
     if (k == 1) {
         Seg s{};
         s.op = OP_ATOM; s.kind = SEG_UNARY; s.a_begin = 0; s.a_count = (uint64_t)n_props;
-        s.n_tiles = (s.a_count + kTileU - 1) / kTileU;
-        add(s);
+        segs[n++] = s;
         close_group(OP_ATOM, 0);
         return n;
     }
@@ -429,8 +491,7 @@ int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, Seg *segs
             if (cnt) {
                 Seg s{};
                 s.op = op; s.kind = SEG_UNARY; s.a_begin = c->lvl_begin[k - 1]; s.a_count = cnt;
-                s.n_tiles = (cnt + kTileU - 1) / kTileU;
-                add(s);
+                segs[n++] = s;
             }
             close_group(op, first);
             continue;
@@ -438,23 +499,17 @@ int build_segments(const ltl_ctx *c, int k, uint32_t ops, int n_props, Seg *segs
         for (int cl = 1; cl <= k - 2; ++cl) {
             const int cr = k - 1 - cl;
             if (op != OP_U && cl > cr) continue;
-            const uint64_t na = c->lvl_count[cl], nb = c->lvl_count[cr];
-            if (!na || !nb) continue;
+            const uint64_t na = c->lvl_count[cl], nbb = c->lvl_count[cr];
+            if (!na || !nbb) continue;
             Seg s{};
-            s.op = op; s.a_begin = c->lvl_begin[cl]; s.a_count = na; s.b_begin = c->lvl_begin[cr]; s.b_count = nb;
+            s.op = op; s.a_begin = c->lvl_begin[cl]; s.a_count = na; s.b_begin = c->lvl_begin[cr]; s.b_count = nbb;
             if (op != OP_U && cl == cr) {
                 if (na < 2) continue;
                 s.kind = SEG_TRI;
-                s.n_ta = s.n_tb = (uint32_t)((na + kTileA - 1) / kTileA);
-                s.n_tiles = (uint64_t)s.n_ta * (s.n_ta + 1) / 2;
             } else {
                 s.kind = SEG_RECT;
-                s.n_ta = (uint32_t)((na + kTileA - 1) / kTileA);
-                s.n_tb = (uint32_t)((nb + kTileB - 1) / kTileB);
-                s.n_tiles = (uint64_t)s.n_ta * s.n_tb;
-                s.a_inner = s.n_ta <= s.n_tb ? 1 : 0;
             }
-            add(s);
+            segs[n++] = s;
         }
         close_group(op, first);
     }
@@ -561,8 +616,12 @@ ltl_status run_learn(ltl_ctx *c, const uint32_t *d_letters_in, const uint64_t *d
     CUDA_TRY(cudaMemsetAsync(ws + L.o_hvals, 0xff, 4 * L.hslots, sm));
     CUDA_TRY(cudaMemsetAsync(d_mask, 0, 8 * L.stride, sm));
     CUDA_TRY(cudaMemsetAsync(d_atoms, 0, 8 * L.stride * (uint64_t)n_props, sm));
-    CUDA_TRY(launch_pack(d_letters, d_offsets, (uint32_t)T, L.plane, L.W, n_props, d_mask, d_atoms, L.stride, d_ctrl,
-                         sm));
+    if (L.narrow)
+        CUDA_TRY(launch_pack_narrow(d_letters, d_offsets, (uint32_t)T, L.plane, n_props, d_mask, d_atoms, L.stride,
+                                    d_ctrl, sm));
+    else
+        CUDA_TRY(launch_pack(d_letters, d_offsets, (uint32_t)T, L.plane, L.W, n_props, d_mask, d_atoms, L.stride,
+                             d_ctrl, sm));
     CUDA_TRY(launch_keys(d_keys, L.stride, kKeySeed, sm));
     st.launches += 2;
 
@@ -597,7 +656,8 @@ ltl_status run_learn(ltl_ctx *c, const uint32_t *d_letters_in, const uint64_t *d
     OpGroup groups[8];
     for (int k = 1; k <= max_size; ++k) {
         int n_groups = 0;
-        const int n_segs = build_segments(c, k, ops, n_props, c->h_segs, groups, n_groups);
+        const int n_segs = build_segments(c, k, ops, n_props, (uint64_t)blocks_per_sm * (uint64_t)c->n_sm, L.NB,
+                                          c->h_segs, groups, n_groups);
         c->lvl_begin[k] = prev_entries;
         if (n_segs == 0 || n_groups == 0) {
             // no candidate of this size (e.g. no connective allowed): the level is empty
@@ -631,6 +691,7 @@ ltl_status run_learn(ltl_ctx *c, const uint32_t *d_letters_in, const uint64_t *d
         st.ms[k] = ms;
         if (h.invalid_letter) return fail(LTL_ERR_INVALID, "trace letters use propositions >= n_props, offsets "
                                                            "decrease, or a trace exceeds max_len");
+        if (h.err == LTL_ERR_INVALID) return fail(LTL_ERR_INVALID, "launch shape / shared memory mismatch");
         if (h.err) return fail((ltl_status)h.err, "device wait exceeded spin_limit (%llu timeouts)",
                                (unsigned long long)h.timeouts);
         const uint64_t ent = std::min<uint64_t>(h.n_entries, L.max_entries);
@@ -651,7 +712,8 @@ ltl_status run_learn(ltl_ctx *c, const uint32_t *d_letters_in, const uint64_t *d
     st.threads_per_cta = (uint32_t)L.NT;
     st.batch = (uint32_t)L.NB;
     st.ctas_per_sm = (uint32_t)blocks_per_sm;
-    st.traces_per_thread = (uint32_t)(2 * L.C);
+    st.traces_per_thread = (uint32_t)(L.narrow ? 4 * L.C : 2 * L.C);
+    st.traces_per_word = L.narrow ? 2u : 1u;
     st.chunk_groups = L.G;
     st.max_entries = L.max_entries;
     st.d2h_bytes += 0;
@@ -816,6 +878,17 @@ ltl_status ltl_ctx_entry(ltl_ctx *c, uint64_t idx, char *formula_out, size_t for
         ltl_status s = formula_of(c, p, n_ent, text);
         if (s != LTL_OK) return s;
         if ((s = write_formula(text, formula_out, formula_cap)) != LTL_OK) return s;
+    }
+    if (cs_out && L.narrow) {
+        if (words_per_trace != 1) return fail(LTL_ERR_INVALID, "words_per_trace must be 1");
+        // word q of the plane holds traces 2q (low half) and 2q + 1 (high half)
+        const uint64_t nw = ((uint64_t)L.n_traces + 1) / 2;
+        std::vector<uint64_t> words(nw ? nw : 1);
+        CUDA_TRY(cudaMemcpyAsync(words.data(), c->ws + L.o_arena + 8 * L.stride * idx, 8 * nw, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        for (uint64_t t = 0; t < L.n_traces; ++t) cs_out[t] = (words[t / 2] >> (32 * (t & 1))) & 0xffffffffull;
+        return LTL_OK;
     }
     if (cs_out) {
         if (words_per_trace != L.W) return fail(LTL_ERR_INVALID, "words_per_trace must be %d", L.W);

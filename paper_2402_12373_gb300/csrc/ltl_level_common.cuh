@@ -60,53 +60,119 @@ __device__ __forceinline__ void load_frag(const uint64_t *base, uint64_t plane, 
     }
 }
 
-// The connective itself (Section 4): a = left operand (or the only one),
-// b = right operand; the result replaces r.  m is the length mask.
-template <int OP, int W, int C>
+// Narrow layout: one uint64 word holds two traces of at most 32 positions
+// (bits 0..31: the even trace, bits 32..63: the odd one).  A shift toward
+// position 0 then acts on each 32-bit half separately.
+__device__ __forceinline__ uint64_t shr_narrow(uint64_t x, uint32_t s) {
+    const uint32_t lo = (uint32_t)x >> s, hi = (uint32_t)(x >> 32) >> s;
+    return ((uint64_t)hi << 32) | (uint64_t)lo;
+}
+
+template <int W, bool NARROW>
+__device__ __forceinline__ void shr_any(const uint64_t (&cs)[W], uint32_t s, uint64_t (&out)[W]) {
+    if (NARROW) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) out[w] = shr_narrow(cs[w], s);
+    } else {
+        shr<W>(cs, s, out);
+    }
+}
+
+// The connective itself (Section 4) on all of a thread's traces at once: a =
+// left operand (or the only one), r = right operand on entry for binary
+// connectives, the result on exit; m = length mask (Not and G).  The
+// exponential-propagation loops run step-outer, trace-inner, so each shift
+// step issues 2 * C * W independent updates.
+template <int OP, int W, int C, bool NARROW = false>
 __device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Frag<W, C> &m, int nsteps) {
+    if (OP == OP_ATOM || OP == OP_X || OP == OP_F || OP == OP_G || OP == OP_NOT) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
+        for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            if (OP == OP_ATOM) {
+            for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
-            } else if (OP == OP_NOT) {
+                for (int w = 0; w < W; ++w)
+                    r.v[c][j][w] = (OP == OP_NOT || OP == OP_G) ? (m.v[c][j][w] & ~a.v[c][j][w]) : a.v[c][j][w];
+    }
+    if (OP == OP_X) {
 #pragma unroll
-                for (int w = 0; w < W; ++w) r.v[c][j][w] = m.v[c][j][w] & ~a.v[c][j][w];
-            } else if (OP == OP_X) {
+        for (int c = 0; c < C; ++c)
 #pragma unroll
-                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
-                op_x<W>(r.v[c][j]);
-            } else if (OP == OP_F) {
+            for (int j = 0; j < 2; ++j) {
+                uint64_t t[W];
+                shr_any<W, NARROW>(r.v[c][j], 1u, t);
 #pragma unroll
-                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
-                op_f<W>(r.v[c][j], nsteps);
-            } else if (OP == OP_G) {
-#pragma unroll
-                for (int w = 0; w < W; ++w) r.v[c][j][w] = a.v[c][j][w];
-                op_g<W>(r.v[c][j], m.v[c][j], nsteps);
-            } else if (OP == OP_AND) {
-#pragma unroll
-                for (int w = 0; w < W; ++w) r.v[c][j][w] &= a.v[c][j][w];
-            } else if (OP == OP_OR) {
-#pragma unroll
-                for (int w = 0; w < W; ++w) r.v[c][j][w] |= a.v[c][j][w];
-            } else if (OP == OP_U) {
-                op_u<W>(a.v[c][j], r.v[c][j], nsteps);   // r holds the right operand on entry
+                for (int w = 0; w < W; ++w) r.v[c][j][w] = t[w];
             }
+    } else if (OP == OP_F || OP == OP_G) {
+        for (int i = 0; i < nsteps; ++i) {
+            const uint32_t s = 1u << i;
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    uint64_t t[W];
+                    shr_any<W, NARROW>(r.v[c][j], s, t);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) r.v[c][j][w] |= t[w];
+                }
+        }
+        if (OP == OP_G) {   // G f = not F not f within the trace
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int w = 0; w < W; ++w) r.v[c][j][w] = m.v[c][j][w] & ~r.v[c][j][w];
+        }
+    } else if (OP == OP_AND || OP == OP_OR) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    r.v[c][j][w] = (OP == OP_AND) ? (r.v[c][j][w] & a.v[c][j][w]) : (r.v[c][j][w] | a.v[c][j][w]);
+    } else if (OP == OP_U) {
+        // a: "f holds on [j, j + 2^i)"; r: "f U g within 2^i" (Lemma 2)
+        for (int i = 0; i < nsteps; ++i) {
+            const uint32_t s = 1u << i;
+            const bool last = (i + 1 == nsteps);
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    uint64_t t[W];
+                    shr_any<W, NARROW>(r.v[c][j], s, t);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) r.v[c][j][w] |= a.v[c][j][w] & t[w];
+                    if (!last) {
+                        shr_any<W, NARROW>(a.v[c][j], s, t);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) a.v[c][j][w] &= t[w];
+                    }
+                }
         }
     }
 }
 
-// Soundness bits of this thread's traces: bit (2c + j) = value at position 0.
-template <int W, int C>
+// Soundness bits of this thread's traces: the value at position 0 of trace
+// slot (c, j) is bit 2c + j; in the narrow layout word (c, j) holds two
+// traces, at bits 4c + 2j (even trace) and 4c + 2j + 1 (odd trace).
+template <int W, int C, bool NARROW = false>
 __device__ __forceinline__ uint32_t pos0_bits(const Frag<W, C> &r) {
     uint32_t b = 0;
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) b |= ((uint32_t)r.v[c][j][0] & 1u) << (2 * c + j);
+        for (int j = 0; j < 2; ++j) {
+            if (NARROW) {
+                b |= ((uint32_t)r.v[c][j][0] & 1u) << (4 * c + 2 * j);
+                b |= ((uint32_t)(r.v[c][j][0] >> 32) & 1u) << (4 * c + 2 * j + 1);
+            } else {
+                b |= ((uint32_t)r.v[c][j][0] & 1u) << (2 * c + j);
+            }
+        }
     return b;
 }
 
@@ -221,8 +287,8 @@ __device__ __forceinline__ unsigned long long fp_key(uint64_t s) {
 __device__ __forceinline__ void decode_tile(const Seg &sg, uint64_t k, uint64_t &a0, uint64_t &a1, uint64_t &b0,
                                             uint64_t &b1) {
     if (sg.kind == SEG_UNARY) {
-        a0 = k * kTileU;
-        a1 = min(a0 + kTileU, sg.a_count);
+        a0 = k * sg.ta;
+        a1 = min(a0 + sg.ta, sg.a_count);
         b0 = 0;
         b1 = 1;
         return;
@@ -245,10 +311,10 @@ __device__ __forceinline__ void decode_tile(const Seg &sg, uint64_t k, uint64_t 
         ta = (uint64_t)r;
         tb = ta + ((uint64_t)k - (uint64_t)row_start(r));
     }
-    a0 = ta * kTileA;
-    a1 = min(a0 + kTileA, sg.a_count);
-    b0 = tb * kTileB;
-    b1 = min(b0 + kTileB, sg.b_count);
+    a0 = ta * sg.ta;
+    a1 = min(a0 + sg.ta, sg.a_count);
+    b0 = tb * sg.tb;
+    b1 = min(b0 + sg.tb, sg.b_count);
 }
 
 __device__ __forceinline__ int find_segment(const LevelArgs &la, unsigned long long tile) {

@@ -81,71 +81,7 @@ struct LaneConst {
     int tid, lane, warp, nwarps;
 };
 
-// One thread's pair of traces (t0, t0 + 1) of one candidate: operands from
-// shared memory (pa: left / only operand, pb_: right operand of a binary
-// connective), the length mask from global memory (NOT and G only).
-template <int OP, int W>
-__device__ __forceinline__ void compute_pair(const uint64_t *pa, const uint64_t *pb_, const uint64_t *pm,
-                                             uint64_t plane, int nsteps, uint64_t (&out)[2][W]) {
-    constexpr bool BIN = is_binary(OP);
-    constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
-    uint64_t a[2][W];
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pa + (uint64_t)w * plane);
-        a[0][w] = q.x;
-        a[1][w] = q.y;
-    }
-    if (BIN) {
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pb_ + (uint64_t)w * plane);
-            out[0][w] = q.x;
-            out[1][w] = q.y;
-        }
-    }
-    uint64_t m[2][W];
-    if (MASKED) {
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const ulonglong2 q = __ldg(reinterpret_cast<const ulonglong2 *>(pm + (uint64_t)w * plane));
-            m[0][w] = q.x;
-            m[1][w] = q.y;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        if (OP == OP_ATOM) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
-        } else if (OP == OP_NOT) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) out[j][w] = m[j][w] & ~a[j][w];
-        } else if (OP == OP_X) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
-            op_x<W>(out[j]);
-        } else if (OP == OP_F) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
-            op_f<W>(out[j], nsteps);
-        } else if (OP == OP_G) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) out[j][w] = a[j][w];
-            op_g<W>(out[j], m[j], nsteps);
-        } else if (OP == OP_AND) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) out[j][w] &= a[j][w];
-        } else if (OP == OP_OR) {
-#pragma unroll
-            for (int w = 0; w < W; ++w) out[j][w] |= a[j][w];
-        } else if (OP == OP_U) {
-            op_u<W>(a[j], out[j], nsteps);
-        }
-    }
-}
-
-template <int W, int C, int NB, int OP>
+template <int W, int C, int NB, int OP, bool NARROW>
 __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0, uint64_t a1,
                                            uint64_t b0, uint64_t b1, FusedShared<NB> &sh, uint64_t *slots,
                                            uint32_t &phase, uint32_t &round, const LaneConst &lc,
@@ -218,6 +154,7 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
     while (have) {
         wait_data();
         // ---- 2. candidates of the batch in registers
+        constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
         Frag<W, C> r[NB];
         uint64_t fp[NB];
         uint32_t badm = 0;
@@ -225,13 +162,12 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
         for (int k = 0; k < NB; ++k) {
             fp[k] = 0;
             if (k < nb) {
-                const uint64_t *sa = slots + (uint64_t)(BIN ? NB : k) * lc.stride + lc.toff;
-                const uint64_t *sb = slots + (uint64_t)k * lc.stride + lc.toff;
-#pragma unroll
-                for (int c = 0; c < C; ++c)
-                    compute_pair<OP, W>(sa + c * lc.cs, sb + c * lc.cs, pb.mask + lc.toff + c * lc.cs, lc.plane,
-                                        pb.nsteps, r[k].v[c]);
-                const uint32_t bits = pos0_bits<W, C>(r[k]);
+                Frag<W, C> x, m;
+                load_frag<W, C, false>(slots + (uint64_t)(BIN ? NB : k) * lc.stride, lc.plane, lc.toff, lc.cs, x);
+                if (BIN) load_frag<W, C, false>(slots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
+                if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
+                apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps);
+                const uint32_t bits = pos0_bits<W, C, NARROW>(r[k]);
                 badm |= (((bits ^ lc.want) & lc.care) != 0u ? 1u : 0u) << k;
             }
         }
@@ -368,8 +304,10 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
 
 }  // namespace
 
-template <int W, int C, int NB, int OP>
-__global__ void __launch_bounds__(256, 2) fused_level_kernel(Problem pb, LevelArgs la) {
+// Register cap: 168 for 8 words per thread (three 128-thread CTAs per SM),
+// 128 for smaller shapes (at most 256 threads per CTA either way).
+template <int W, int C, int NB, int OP, bool NARROW>
+__global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(Problem pb, LevelArgs la) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     uint64_t *slots = reinterpret_cast<uint64_t *>(dyn_smem);
     __shared__ FusedShared<NB> sh;
@@ -388,10 +326,26 @@ __global__ void __launch_bounds__(256, 2) fused_level_kernel(Problem pb, LevelAr
     for (int c = 0; c < C; ++c)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const uint64_t t = lc.toff + c * lc.cs + j;
-            if (t < pb.n_pos) lc.want |= 1u << (2 * c + j);
-            if (t < pb.n_traces) lc.care |= 1u << (2 * c + j);
+            const uint64_t word = lc.toff + c * lc.cs + j;
+            if (NARROW) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t t = 2 * word + h;
+                    if (t < pb.n_pos) lc.want |= 1u << (4 * c + 2 * j + h);
+                    if (t < pb.n_traces) lc.care |= 1u << (4 * c + 2 * j + h);
+                }
+            } else {
+                if (word < pb.n_pos) lc.want |= 1u << (2 * c + j);
+                if (word < pb.n_traces) lc.care |= 1u << (2 * c + j);
+            }
         }
+    // the operand slots must fit the dynamic shared memory this launch got
+    uint32_t dsmem;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsmem));
+    if ((uint64_t)dsmem < (uint64_t)(NB + 1) * pb.stride * 8ull) {
+        if (lc.tid == 0) atomicCAS(&pb.ctrl->err, 0, -1 /* LTL_ERR_INVALID */);
+        return;
+    }
     if (lc.tid == 0) {
         mbar_init(&sh.bar, 1);
         sh.neq[0] = sh.neq[1] = 0u;
@@ -412,31 +366,32 @@ __global__ void __launch_bounds__(256, 2) fused_level_kernel(Problem pb, LevelAr
         const Seg sg = la.segs[find_segment(la, tile)];
         uint64_t a0, a1, b0, b1;
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
-        fused_tile<W, C, NB, OP>(pb, la.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done);
+        fused_tile<W, C, NB, OP, NARROW>(pb, la.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done);
     }
     if (lc.tid == 0 && done) atomicAdd(&pb.ctrl->cands, done);
 }
 
 }  // namespace lvl
 
-// candidates per batch: 2 when a thread holds 8 words per candidate, else 4
-template <int W, int C>
+// candidates per batch: 2 when a thread holds 8 words per candidate or uses
+// the narrow layout (two traces per word), else 4
+template <int W, int C, bool NARROW>
 struct FusedNB {
-    static constexpr int value = (W * C >= 8) ? 2 : 4;
+    static constexpr int value = (NARROW || W * C >= 8) ? 2 : 4;
 };
 
-template <int W, int C>
+template <int W, int C, bool NARROW = false>
 const void *fused_fn(int op) {
-    constexpr int NB = FusedNB<W, C>::value;
+    constexpr int NB = FusedNB<W, C, NARROW>::value;
     switch (op) {
-    case OP_ATOM: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_ATOM>);
-    case OP_NOT: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_NOT>);
-    case OP_AND: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_AND>);
-    case OP_OR: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_OR>);
-    case OP_X: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_X>);
-    case OP_F: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_F>);
-    case OP_G: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_G>);
-    case OP_U: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_U>);
+    case OP_ATOM: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_ATOM, NARROW>);
+    case OP_NOT: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_NOT, NARROW>);
+    case OP_AND: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_AND, NARROW>);
+    case OP_OR: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_OR, NARROW>);
+    case OP_X: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_X, NARROW>);
+    case OP_F: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_F, NARROW>);
+    case OP_G: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_G, NARROW>);
+    case OP_U: return reinterpret_cast<const void *>(&lvl::fused_level_kernel<W, C, NB, OP_U, NARROW>);
     default: return nullptr;
     }
 }

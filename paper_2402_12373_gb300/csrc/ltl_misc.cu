@@ -52,6 +52,47 @@ __global__ void pack_kernel(const uint32_t *__restrict__ letters, const uint64_t
     if (n_props < 32 && (seen >> n_props)) atomicExch(&ctrl->invalid_letter, 1);
 }
 
+// Narrow layout (every trace at most 32 long): word q of a plane holds traces
+// 2q (bits 0..31) and 2q + 1 (bits 32..63).  One thread per word.
+__global__ void pack_narrow_kernel(const uint32_t *__restrict__ letters, const uint64_t *__restrict__ offsets,
+                                   uint32_t n_traces, uint64_t plane, int n_props, uint64_t *mask, uint64_t *atoms,
+                                   uint64_t stride, Ctrl *ctrl) {
+    const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= plane) return;
+    uint64_t off[2] = {0, 0}, len[2] = {0, 0};
+    for (int h = 0; h < 2; ++h) {
+        const uint64_t t = 2 * q + h;
+        if (t < n_traces) {
+            off[h] = offsets[t];
+            const uint64_t end = offsets[t + 1];
+            if (end < off[h] || (t == 0 && off[h] != 0)) {
+                atomicExch(&ctrl->invalid_letter, 1);
+                return;
+            }
+            len[h] = end - off[h];
+            if (len[h] > 32) {
+                atomicExch(&ctrl->invalid_letter, 1);
+                len[h] = 32;
+            }
+        }
+    }
+    uint64_t mk = 0;
+    for (int h = 0; h < 2; ++h) mk |= (len[h] == 32 ? 0xffffffffull : ((1ull << len[h]) - 1ull)) << (32 * h);
+    mask[q] = mk;
+    uint32_t seen = 0;
+    for (int p = 0; p < n_props; ++p) {
+        uint64_t bits = 0;
+        for (int h = 0; h < 2; ++h)
+            for (uint64_t i = 0; i < len[h]; ++i) {
+                const uint32_t l = letters[off[h] + i];
+                seen |= l;
+                bits |= (uint64_t)((l >> p) & 1u) << (32 * h + i);
+            }
+        atoms[(uint64_t)p * stride + q] = bits;
+    }
+    if (n_props < 32 && (seen >> n_props)) atomicExch(&ctrl->invalid_letter, 1);
+}
+
 // NH keys, one per word of a matrix: SplitMix64 outputs of a fixed seed.
 __global__ void keys_kernel(uint64_t *keys, uint64_t n, uint64_t seed) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,6 +217,15 @@ cudaError_t launch_pack(const uint32_t *letters, const uint64_t *offsets, uint32
     const int th = 256;
     pack_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(letters, offsets, n_traces, plane, W, n_props, mask,
                                                              atoms, stride, ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_narrow(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
+                               int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
+                               cudaStream_t s) {
+    const int th = 256;
+    pack_narrow_kernel<<<(unsigned)((plane + th - 1) / th), th, 0, s>>>(letters, offsets, n_traces, plane, n_props,
+                                                                        mask, atoms, stride, ctrl);
     return cudaGetLastError();
 }
 

@@ -21,8 +21,10 @@ __host__ __device__ inline int prov_op(uint64_t p) { return (int)(p >> 60); }
 __host__ __device__ inline uint64_t prov_a(uint64_t p) { return (p >> 30) & ((1ull << 30) - 1); }
 __host__ __device__ inline uint64_t prov_b(uint64_t p) { return p & ((1ull << 30) - 1); }
 
-// Candidate tiles: rectangular tiles of kTileA x kTileB (left x right operand)
-// pairs; unary segments are cut into runs of kTileU operands.
+// Candidate tiles: rectangular tiles of up to kTileA x kTileB (left x right
+// operand) pairs; unary segments are cut into runs of up to kTileU operands.
+// The host shrinks tiles when a launch has few candidates, so that every
+// resident CTA gets work.
 constexpr int kTileA = 8;
 constexpr int kTileB = 8;
 constexpr int kTileU = 16;
@@ -41,6 +43,7 @@ struct Seg {
     uint64_t n_tiles;
     uint32_t n_ta, n_tb;   // tiles along a and along b
     int32_t a_inner;       // RECT: 1 = a-tile index varies fastest
+    uint32_t ta, tb;       // tile extent along a (unary: run length) and along b
     int32_t pad;
 };
 

@@ -235,3 +235,34 @@ def test_cap_reached_with_small_budget(ws):
     want = O.learn(s.P, s.N, 3, max_size=got["levels_done"], stop_mode=0)
     d = got["levels_done"]
     assert got["unique"][1:d + 1] == want["unique"][1:d + 1]
+
+
+def _long_traces(seed, n_each, lo, hi, n_props=2):
+    rng = random.Random(seed)
+    mk = lambda: [rng.randrange(1 << n_props) for _ in range(rng.randrange(lo, hi + 1))]
+    return _ts([mk() for _ in range(n_each)]), _ts([mk() for _ in range(n_each)])
+
+
+@pytest.mark.parametrize("max_chunks", [0, 1, 2, 4, 8])
+def test_launch_shapes_narrow_and_wide(ws, max_chunks):
+    """Every launch shape the planner can pick gives the oracle's counts:
+    narrow (traces <= 32) and wide (33..64) layouts, CTAs of 32..256 threads,
+    fused and two-pass."""
+    s = synth.single_large(n_each=2048)                 # 4096 traces, narrow
+    P2, N2 = _long_traces(5, 2048, 33, 64)               # 4096 traces, wide W = 1
+    for (P, N, n_props, K) in ((s.P, s.N, 3, 4), (P2, N2, 2, 4)):
+        with L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=max_chunks) as ctx:
+            got = ctx.learn(P, N, n_props, max_size=K)
+        want = _oracle_cached(P, N, n_props, K)
+        assert got["unique"][1:K + 1] == want["unique"][1:K + 1], (max_chunks, got["threads_per_cta"])
+        assert got["candidates"][1:K + 1] == want["candidates"][1:K + 1]
+
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_cached(P, N, n_props, K):
+    key = (P.letters.tobytes(), P.offsets.tobytes(), N.letters.tobytes(), N.offsets.tobytes(), n_props, K)
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = O.learn(P, N, n_props, max_size=K, stop_mode=0)
+    return _ORACLE_CACHE[key]
