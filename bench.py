@@ -69,6 +69,30 @@ def level_bytes(stats, k, T, n_props):
     return (unary * 2 + binary * 3) * T * per_trace
 
 
+OP_NAMES = ["atoms", "not", "and", "or", "X", "F", "G", "U"]
+
+
+def op_candidates(unique, k, op, n_props):
+    """Candidates of connective `op` at size k, from the unique counts of the
+    smaller sizes (the candidate space of the paper's handleOp, as read here:
+    unary over size k-1; U over ordered splits and pairs; And/Or over splits
+    i <= j, pairs a < b when i == j)."""
+    if k == 1 or op == 0:
+        return n_props if (k == 1 and op == 0) else 0
+    if op in (1, 4, 5, 6):
+        return unique[k - 1]
+    tot = 0
+    for i in range(1, k - 1):
+        j = k - 1 - i
+        if op == 7:
+            tot += unique[i] * unique[j]
+        elif i < j:
+            tot += unique[i] * unique[j]
+        elif i == j:
+            tot += unique[i] * (unique[i] - 1) // 2
+    return tot
+
+
 def kernel_sources_sha():
     h = hashlib.sha256()
     for f in ("ltl_level_fused.cuh", "ltl_level_common.cuh", "ltl_device.cuh", "ltl_types.h"):
@@ -289,18 +313,27 @@ def main():
     r0 = results[-1]
     W = r0["words_per_trace"]
 
-    # dominant kernel: the level launch with the longest device time
-    kd = max(range(1, r0["levels_done"] + 1), key=lambda k: sum(r["ms"][k] for r in results))
-    kd_ms = statistics.mean(r["ms"][kd] for r in results)
-    kd_bytes = level_bytes(r0, kd, T, spec.n_props)
+    # dominant kernel: the (size level, connective) launch with the longest
+    # device time (CUDA events the library records on its stream)
+    pairs = [(k, o) for k in range(1, r0["levels_done"] + 1) for o in range(8)]
+    kd, od = max(pairs, key=lambda ko: sum(r["op_ms"][ko[0]][ko[1]] for r in results))
+    kd_ms = statistics.mean(r["op_ms"][kd][od] for r in results)
+    per_trace = 4 if r0["traces_per_word"] == 2 else 8 * W
+    n_operands = 2 if od in (2, 3, 7) else 1
+    kd_cands = op_candidates(r0["unique"], kd, od, spec.n_props)
+    kd_bytes = kd_cands * (n_operands + 1) * T * per_trace
     peaks, peak_src = measured_peaks()
     achieved = kd_bytes / (kd_ms / 1e3) / 1e9
     sha = kernel_sources_sha()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(sha),
-                "kernel": "level_kernel<W=%d>, size level %d" % (W, kd), "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": kd_bytes, "launch_ms": kd_ms,
-                "candidates_per_launch": r0["candidates"][kd], "kernel_sources_sha": sha}
+                "kernel": "fused_level_kernel connective %s, size level %d (%s layout)"
+                          % (OP_NAMES[od], kd, "narrow" if r0["traces_per_word"] == 2 else "wide"),
+                "peak_source": peak_src + " (hbm_gbs, copy bandwidth)",
+                "algorithmic_bytes_per_launch": kd_bytes, "bytes_per_candidate_trace": (n_operands + 1) * per_trace,
+                "candidates_per_launch": kd_cands, "launch_ms": kd_ms,
+                "level_ms": statistics.mean(r["ms"][kd] for r in results),
+                "kernel_sources_sha": sha}
 
     # end to end: host trace buffers through ltl_ctx_learn
     e2e_times, e2e_units, h2d, d2h = [], 0, 0, 0

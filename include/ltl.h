@@ -118,6 +118,10 @@ typedef struct {
     uint64_t h2d_bytes, d2h_bytes;        /* host<->device bytes copied         */
     uint64_t max_entries;                 /* cache capacity in entries          */
     double total_ms;                      /* wall time of the call              */
+    float op_ms[LTL_MAX_LEVELS][8];       /* device time of each connective's
+                                             launch: [level][op], op = 0 atoms,
+                                             1 Not, 2 And, 3 Or, 4 X, 5 F, 6 G,
+                                             7 U                               */
 } ltl_stats;
 
 /* ---------------------------------------------------------------------------
@@ -188,6 +192,66 @@ ltl_status ltl_ctx_level_range(ltl_ctx *ctx, int level, uint64_t *begin, uint64_
  * small. */
 ltl_status ltl_ctx_entry(ltl_ctx *ctx, uint64_t idx, char *formula_out, size_t formula_cap,
                          uint64_t *cs_out, int words_per_trace);
+
+/* ---------------------------------------------------------------------------
+ * Batched and served learning.  Many independent learning problems share one
+ * device workspace; each keeps its language cache and hash set resident in
+ * its own region of the workspace while it runs.  Work advances in rounds:
+ * in one round every resident problem enumerates its next size level, and the
+ * candidates of all of them are processed by one launch per connective and
+ * launch shape (persistent CTAs pull tiles of any problem).  Problems are
+ * admitted into free memory between rounds, so problems that arrive while
+ * others run join the next round (continuous batching).  Each problem's result
+ * is the same as ltl_learn's on it alone: same status, minimal size and
+ * per-level counts (the formula text may be another minimal separator).
+ * The paper has no batching; its D&C unit notes that sub-problems can be
+ * learned in parallel (Section 6).
+ * -------------------------------------------------------------------------*/
+#define LTL_FORMULA_MAX 512
+
+typedef struct {
+    ltl_traces P, N;              /* host traces (copied at submission)        */
+    int n_props;
+    uint32_t ops;
+    int max_size;
+    uint64_t mem_budget_bytes;    /* device bytes for this problem's cache and
+                                     hash set; 0 = the engine's default share  */
+} ltl_problem;
+
+typedef struct {
+    uint64_t id;                  /* submission id (batch: the input index)    */
+    ltl_status status;            /* as ltl_learn; LTL_ERR_OOM if the budget
+                                     exceeds the whole workspace               */
+    int found_size;
+    int levels_done;
+    char formula[LTL_FORMULA_MAX];
+    uint64_t unique[LTL_MAX_LEVELS];
+    uint64_t candidates[LTL_MAX_LEVELS];
+    uint64_t n_traces;
+    uint32_t rounds;              /* rounds the problem took part in           */
+    double queue_ms;              /* submission -> admission                   */
+    double latency_ms;            /* submission -> result                      */
+} ltl_result;
+
+/* Learns n problems together; out[i] is problem i's result.  opts as for
+ * ltl_learn (stop_on_solution applies to every problem; opts->workspace, if
+ * given, holds all of them).  Returns LTL_OK if every problem was processed
+ * (look at out[i].status), or an error. */
+ltl_status ltl_learn_batch(int n, const ltl_problem *problems, const ltl_opts *opts, ltl_result *out);
+
+/* A learning server: a host worker thread runs rounds while problems are
+ * resident and admits submitted problems between rounds as their memory
+ * budget fits (max_resident caps how many are resident at once, <= 4096). */
+typedef struct ltl_server ltl_server;
+ltl_status ltl_server_create(const ltl_opts *opts, int max_resident, ltl_server **out);
+/* Queues a problem (its traces are copied); *id receives its id. */
+ltl_status ltl_server_submit(ltl_server *srv, const ltl_problem *problem, uint64_t *id);
+/* Moves up to max finished results into out (in completion order), waiting up
+ * to wait_ms milliseconds for at least one; *n_out receives the count. */
+ltl_status ltl_server_poll(ltl_server *srv, ltl_result *out, int max, int *n_out, int wait_ms);
+/* Number of problems queued or resident (not yet polled as results). */
+ltl_status ltl_server_pending(ltl_server *srv, uint64_t *queued, uint64_t *resident);
+void ltl_server_destroy(ltl_server *srv);
 
 /* ---------------------------------------------------------------------------
  * ltl_eval_noalloc -- ltl_eval for callers that cannot allocate device memory.

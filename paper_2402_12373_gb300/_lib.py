@@ -27,7 +27,9 @@ MAX_LEVELS = 64
 # Every symbol include/ltl.h declares.
 EXPORTS = ["ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_destroy", "ltl_ctx_learn",
            "ltl_ctx_learn_device", "ltl_ctx_level_range", "ltl_ctx_entry", "ltl_last_error",
-           "ltl_version", "ltl_eval_noalloc"]
+           "ltl_version", "ltl_eval_noalloc", "ltl_learn_batch", "ltl_server_create",
+           "ltl_server_submit", "ltl_server_poll", "ltl_server_pending", "ltl_server_destroy"]
+FORMULA_MAX = 512
 
 
 class LtlError(RuntimeError):
@@ -62,7 +64,8 @@ class Stats(ctypes.Structure):
                 ("traces_per_word", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("launches", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
-                ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+                ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("op_ms", (ctypes.c_float * 8) * MAX_LEVELS)]
 
     def to_dict(self, max_size: int) -> Dict:
         K = max_size
@@ -79,7 +82,29 @@ class Stats(ctypes.Structure):
             "launches": int(self.launches), "h2d_bytes": int(self.h2d_bytes),
             "d2h_bytes": int(self.d2h_bytes), "max_entries": int(self.max_entries),
             "total_ms": float(self.total_ms),
+            "op_ms": [[float(self.op_ms[c][o]) for o in range(8)] for c in range(K + 1)],
         }
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("P", Traces), ("N", Traces), ("n_props", ctypes.c_int), ("ops", ctypes.c_uint32),
+                ("max_size", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("found_size", ctypes.c_int),
+                ("levels_done", ctypes.c_int), ("formula", ctypes.c_char * FORMULA_MAX),
+                ("unique", ctypes.c_uint64 * MAX_LEVELS), ("candidates", ctypes.c_uint64 * MAX_LEVELS),
+                ("n_traces", ctypes.c_uint64), ("rounds", ctypes.c_uint32), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+    def to_dict(self) -> Dict:
+        st = int(self.status)
+        return {"id": int(self.id), "status": STATUS.get(st, st), "size": int(self.found_size) if st == 0 else None,
+                "formula": self.formula.decode() if st == 0 else None, "levels_done": int(self.levels_done),
+                "unique": [int(x) for x in self.unique], "candidates": [int(x) for x in self.candidates],
+                "n_traces": int(self.n_traces), "rounds": int(self.rounds), "queue_ms": float(self.queue_ms),
+                "latency_ms": float(self.latency_ms)}
 
 
 _lib = None
@@ -116,6 +141,18 @@ def load(build_if_missing: bool = True):
     L.ltl_ctx_entry.argtypes = [vp, u64, ctypes.c_char_p, ctypes.c_size_t, vp, i32]
     L.ltl_eval_noalloc.argtypes = [ctypes.c_char_p, vp, vp, u64, u32, i32, vp, i32, vp]
     L.ltl_eval_noalloc.restype = ctypes.c_int
+    L.ltl_learn_batch.argtypes = [i32, ctypes.POINTER(ProblemDesc), ctypes.POINTER(Opts), ctypes.POINTER(Result)]
+    L.ltl_learn_batch.restype = ctypes.c_int
+    L.ltl_server_create.argtypes = [ctypes.POINTER(Opts), i32, ctypes.POINTER(vp)]
+    L.ltl_server_create.restype = ctypes.c_int
+    L.ltl_server_submit.argtypes = [vp, ctypes.POINTER(ProblemDesc), ctypes.POINTER(u64)]
+    L.ltl_server_submit.restype = ctypes.c_int
+    L.ltl_server_poll.argtypes = [vp, ctypes.POINTER(Result), i32, ctypes.POINTER(i32), i32]
+    L.ltl_server_poll.restype = ctypes.c_int
+    L.ltl_server_pending.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    L.ltl_server_pending.restype = ctypes.c_int
+    L.ltl_server_destroy.argtypes = [vp]
+    L.ltl_server_destroy.restype = None
     L.ltl_last_error.restype = ctypes.c_char_p
     L.ltl_version.restype = ctypes.c_char_p
     for f in ("ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_learn", "ltl_ctx_learn_device",
@@ -291,6 +328,80 @@ def evaluate_noalloc(formula: str, letters, offsets, n_traces: int, max_len: int
                             ctypes.c_void_p(offsets.data_ptr()), n_traces, max_len, n_props,
                             ctypes.c_void_p(out.data_ptr()), words_per_trace, stream)
     _check(rc, ok=(LTL_OK,))
+
+
+def _problem_desc(P, N, n_props: int, ops: int, max_size: int, budget: int = 0):
+    hp, hn = _HostTraces(P), _HostTraces(N)
+    d = ProblemDesc(hp.struct, hn.struct, n_props, ops, max_size, int(budget))
+    return d, (hp, hn)
+
+
+def learn_batch(problems: Sequence, stop: int = STOP_FIRST, workspace=None, mem_budget: int = 0,
+                max_chunks: int = 0) -> List[Dict]:
+    """ltl_learn_batch.  problems: sequence of (P, N, n_props, ops, max_size[, budget])."""
+    L = load()
+    n = len(problems)
+    descs = (ProblemDesc * max(n, 1))()
+    keep = []
+    for i, pr in enumerate(problems):
+        P, N, n_props, ops, max_size = pr[:5]
+        budget = pr[5] if len(pr) > 5 else 0
+        d, k = _problem_desc(P, N, n_props, ops, max_size, budget)
+        descs[i] = d
+        keep.append(k)
+    out = (Result * max(n, 1))()
+    o = _opts(stop, workspace, _current_stream() if workspace is not None else None, mem_budget, 0, max_chunks)
+    _check(L.ltl_learn_batch(n, descs, ctypes.byref(o), out), ok=(LTL_OK,))
+    return [out[i].to_dict() for i in range(n)]
+
+
+class Server:
+    """ltl_server_*: continuous batching of submitted learning problems."""
+
+    def __init__(self, workspace=None, stop: int = STOP_FIRST, max_resident: int = 64, mem_budget: int = 0,
+                 workspace_bytes: Optional[int] = None, max_chunks: int = 0):
+        self._L = load()
+        if workspace is None:
+            workspace = default_workspace(workspace_bytes)
+        self.workspace = workspace
+        self._opts = _opts(stop, workspace, None, mem_budget, 0, max_chunks)
+        h = ctypes.c_void_p()
+        _check(self._L.ltl_server_create(ctypes.byref(self._opts), max_resident, ctypes.byref(h)), ok=(LTL_OK,))
+        self._h = h
+
+    def submit(self, P, N, n_props: int, ops: int = ALL, max_size: int = 7, budget: int = 0) -> int:
+        d, _keep = _problem_desc(P, N, n_props, ops, max_size, budget)
+        i = ctypes.c_uint64()
+        _check(self._L.ltl_server_submit(self._h, ctypes.byref(d), ctypes.byref(i)), ok=(LTL_OK,))
+        return int(i.value)
+
+    def poll(self, max_results: int = 64, wait_ms: int = 0) -> List[Dict]:
+        out = (Result * max_results)()
+        n = ctypes.c_int()
+        _check(self._L.ltl_server_poll(self._h, out, max_results, ctypes.byref(n), wait_ms), ok=(LTL_OK,))
+        return [out[i].to_dict() for i in range(n.value)]
+
+    def pending(self):
+        q, r = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._L.ltl_server_pending(self._h, ctypes.byref(q), ctypes.byref(r)), ok=(LTL_OK,))
+        return int(q.value), int(r.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ltl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def version() -> str:

@@ -1,0 +1,1218 @@
+// ltl_engine.cu -- the host engine: problems resident in a device workspace,
+// advanced size level by size level in rounds (Section 3, `enum`).
+//
+// One round = for every resident problem, the candidate space of its next
+// size level (the segments of Section 3's handleOp: one connective and one
+// split each), grouped by launch shape and connective; one persistent launch
+// per group pulls tiles from any of its problems.  After the round the
+// control blocks of all problems are read back at once, levels are closed,
+// finished problems get their formula rebuilt (one batched provenance walk)
+// and release their memory, and waiting problems are admitted.
+//
+// ltl_ctx_* drive one problem at a time through an engine; ltl_learn_batch
+// and the server drive many.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "ltl_internal.h"
+
+namespace ltl {
+namespace {
+
+constexpr uint64_t kKeySeed = 0x243F6A8885A308D3ull;   // NH key stream seed (digits of pi)
+constexpr int kMaxTokens = 256;
+constexpr int kMaxGroups = 512;                       // launches per round
+
+// Where one problem's device state lives, relative to its region base.
+struct Layout {
+    int W = 0, Wt = 0, C = 0, NT = 0, NB = 1;
+    bool narrow = false;
+    uint32_t G = 0;
+    uint32_t n_traces = 0, n_pos = 0;
+    int n_props = 0, nsteps = 0;
+    uint64_t plane = 0, stride = 0;
+    uint64_t hslots = 0, max_entries = 0;
+    size_t smem = 0;
+    size_t o_letters, o_offsets, o_mask, o_keys, o_atoms, o_hkeys, o_hvals, o_prov, o_arena, end;
+};
+
+// Everything the engine needs to know about one problem's input.
+struct ProblemIn {
+    // host input: positives and negatives (engine-owned copies when `own`)
+    const uint32_t *hl[2] = {nullptr, nullptr};
+    const uint64_t *ho[2] = {nullptr, nullptr};
+    uint64_t hn[2] = {0, 0};
+    std::vector<uint32_t> own_l[2];
+    std::vector<uint64_t> own_o[2];
+    // device input: positives then negatives, one offset array
+    const uint32_t *d_letters = nullptr;
+    const uint64_t *d_offsets = nullptr;
+    bool device_input = false;
+    uint64_t n_pos = 0, n_neg = 0, max_len = 0, total_pos = 0;
+    int n_props = 1;
+    uint32_t ops = LTL_ALL;
+    int max_size = 1;
+    uint64_t budget = 0;
+    uint64_t id = 0;
+    double t_submit = 0;
+};
+
+enum SlotState { SLOT_FREE = 0, SLOT_RUNNING = 1, SLOT_DONE = 2 };
+
+struct Slot {
+    int state = SLOT_FREE;
+    ProblemIn in;
+    Layout L;
+    size_t off = 0, bytes = 0;   // region in the workspace
+    int level = 1;               // next size level to enumerate
+    uint64_t lvl_begin[kMaxLevels] = {}, lvl_count[kMaxLevels] = {};
+    uint64_t prev_entries = 0, prev_cands = 0;
+    bool found = false;
+    ltl_status status = LTL_NOT_FOUND;
+    std::string formula;
+    std::string error;
+    ltl_stats st;
+    uint32_t rounds = 0;
+    double t_admit = 0, t_done = 0;
+};
+
+// First-fit allocator over byte offsets of the workspace.
+struct FreeList {
+    std::map<size_t, size_t> free;   // offset -> size
+    void reset(size_t begin, size_t end) {
+        free.clear();
+        if (end > begin) free[begin] = end - begin;
+    }
+    bool alloc(size_t bytes, size_t &off) {
+        for (auto it = free.begin(); it != free.end(); ++it) {
+            if (it->second >= bytes) {
+                off = it->first;
+                const size_t rest = it->second - bytes;
+                free.erase(it);
+                if (rest) free[off + bytes] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        auto it = free.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free.erase(nx);
+        }
+        if (it != free.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free.erase(it);
+            }
+        }
+    }
+    size_t largest() const {
+        size_t m = 0;
+        for (const auto &kv : free) m = std::max(m, kv.second);
+        return m;
+    }
+};
+
+// Chooses the launch shape of a problem and carves its region for `budget`
+// bytes (0: as many entries as `avail` bytes allow).
+ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint64_t budget, uint64_t avail, Layout &L) {
+    const uint64_t T = in.n_pos + in.n_neg;
+    if (T > 0x7fffffffull) return fail(LTL_ERR_INVALID, "too many traces (%llu)", (unsigned long long)T);
+    L = Layout{};
+    L.n_traces = (uint32_t)T;
+    L.n_pos = (uint32_t)in.n_pos;
+    L.n_props = in.n_props;
+    L.W = (int)std::max<uint64_t>(1, (in.max_len + 63) / 64);
+    L.Wt = (int)pow2_ceil((uint64_t)L.W);
+    if (L.Wt > 8) return fail(LTL_ERR_INVALID, "traces longer than 512 positions are not supported by ltl_learn");
+    L.nsteps = ceil_log2(in.max_len);
+    // Each thread holds C pairs of words (C * W <= 8) of a candidate; a CTA of
+    // up to 256 threads holds a whole matrix (fused kernel); larger matrices
+    // go through the two-pass streaming kernel in `G` chunk groups.  The
+    // narrow layout packs two traces of <= 32 positions per word.
+    const int Cmax = 8 / L.Wt;
+    const uint64_t maxNT = 256;
+    const uint64_t pairs = std::max<uint64_t>(1, (T + 1) / 2);
+    const uint64_t quads = std::max<uint64_t>(1, (T + 3) / 4);
+    const uint64_t cap_c = max_chunks ? pow2_ceil(max_chunks) : 8;
+    const uint64_t ncmax = std::min<uint64_t>(4, cap_c);
+    auto shape = [&](uint64_t units, uint64_t cmax) {
+        uint64_t nt = pow2_ceil((units + cmax - 1) / cmax);
+        nt = std::min<uint64_t>(std::max<uint64_t>(nt, 32), maxNT);
+        L.NT = (int)nt;
+        L.C = (int)std::min<uint64_t>(pow2_ceil((units + nt - 1) / nt), cmax);
+        L.G = 1;
+    };
+    if (in.max_len <= 32 && quads <= maxNT * ncmax) {
+        shape(quads, ncmax);
+        L.narrow = true;
+    } else if (pairs <= maxNT * std::min<uint64_t>(Cmax, cap_c)) {
+        shape(pairs, std::min<uint64_t>(Cmax, cap_c));
+    } else if (pairs <= maxNT * (uint64_t)Cmax) {
+        shape(pairs, (uint64_t)Cmax);
+    } else {
+        L.NT = (int)maxNT;
+        L.C = Cmax;
+        L.G = (uint32_t)((pairs + maxNT * Cmax - 1) / (maxNT * Cmax));
+    }
+    // the batch size the fused kernel of this shape was compiled with (its
+    // shared-memory operand slots are sized from it)
+    L.NB = L.G == 1 ? fused_kernel_batch(L.Wt, L.C, L.narrow) : 1;
+    if (L.G == 1 && L.NB < 1) return fail(LTL_ERR_INVALID, "no fused kernel for W=%d C=%d", L.Wt, L.C);
+    L.plane = (uint64_t)L.G * L.C * 2 * L.NT;   // words per bit-plane
+    L.stride = (uint64_t)L.Wt * L.plane;
+    L.smem = L.G == 1 ? (size_t)(L.NB + 1) * 8 * L.stride : 0;
+
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = o;
+        o = round_up(o + bytes, 256);
+        return r;
+    };
+    L.o_letters = take(in.device_input ? 0 : sizeof(uint32_t) * std::max<uint64_t>(in.total_pos, 1));
+    L.o_offsets = take(in.device_input ? 0 : sizeof(uint64_t) * (T + 1));
+    L.o_mask = take(8 * L.stride);
+    L.o_keys = take(8 * L.stride);
+    L.o_atoms = take(8 * L.stride * (uint64_t)in.n_props);
+    const size_t fixed = o;
+    const uint64_t total = budget ? budget + fixed : avail;
+    if (total <= fixed + 4096) return fail(LTL_ERR_OOM, "memory too small for the problem layout");
+    const uint64_t R = total - fixed - 4096;
+    const uint64_t per = 8 * L.stride + 8;   // arena + provenance per entry
+    uint64_t E = R / (per + 24);
+    uint64_t slots = pow2_ceil(std::max<uint64_t>(2 * E, 1024));
+    while (slots * 12 + E * per > R && E > 0) {
+        E = (R > slots * 12) ? (R - slots * 12) / per : 0;
+        if (slots > 1024 && slots / 2 >= 2 * E) slots /= 2;
+    }
+    E = std::min<uint64_t>(E, kMaxEntries);
+    if (E < 1) return fail(LTL_ERR_OOM, "memory too small for one cache entry");
+    L.max_entries = E;
+    L.hslots = slots;
+    L.o_hkeys = take(8 * slots);
+    L.o_hvals = take(4 * slots);
+    L.o_prov = take(8 * E);
+    L.o_arena = take(8 * L.stride * E);
+    L.end = o;
+    return LTL_OK;
+}
+
+// Tile extents for a launch of `cands` candidates on `slots` resident CTAs:
+// about four tiles per CTA, never fewer than `nb` candidates per tile.
+uint32_t tile_target(uint64_t cands, uint64_t slots, int nb) {
+    uint64_t cpt = cands / std::max<uint64_t>(1, 4 * slots);
+    cpt = std::max<uint64_t>(cpt, (uint64_t)nb);
+    return (uint32_t)std::min<uint64_t>(pow2_ceil(cpt), (uint64_t)kTileA * kTileB);
+}
+
+void set_tiles(Seg &s, uint32_t cpt) {
+    if (s.kind == SEG_UNARY) {
+        s.ta = std::min<uint32_t>(cpt, kTileU);
+        s.tb = 1;
+        s.n_tiles = (s.a_count + s.ta - 1) / s.ta;
+        return;
+    }
+    if (s.kind == SEG_TRI) {
+        uint32_t side = 2;
+        while (side < kTileA && side * side < cpt) side *= 2;
+        s.ta = s.tb = side;
+        s.n_ta = s.n_tb = (uint32_t)((s.a_count + side - 1) / side);
+        s.n_tiles = (uint64_t)s.n_ta * (s.n_ta + 1) / 2;
+        return;
+    }
+    s.tb = std::min<uint32_t>(cpt, kTileB);
+    s.ta = std::max<uint32_t>(1, std::min<uint32_t>(cpt / s.tb, kTileA));
+    s.n_ta = (uint32_t)((s.a_count + s.ta - 1) / s.ta);
+    s.n_tb = (uint32_t)((s.b_count + s.tb - 1) / s.tb);
+    s.n_tiles = (uint64_t)s.n_ta * s.n_tb;
+    s.a_inner = s.n_ta <= s.n_tb ? 1 : 0;
+}
+
+uint64_t seg_candidates(const Seg &s) {
+    if (s.kind == SEG_UNARY) return s.a_count;
+    if (s.kind == SEG_TRI) return s.a_count * (s.a_count - 1) / 2;
+    return s.a_count * s.b_count;
+}
+
+// Candidate space of size level k of one problem (Section 3, handleOp), in
+// the paper's connective order F, U, G, X, And, Or, Not.
+void level_segments(const Slot &s, int k, int prob, std::vector<Seg> &out) {
+    auto push = [&](Seg sg) {
+        sg.prob = prob;
+        sg.level = k;
+        out.push_back(sg);
+    };
+    if (k == 1) {
+        Seg sg{};
+        sg.op = OP_ATOM; sg.kind = SEG_UNARY; sg.a_begin = 0; sg.a_count = (uint64_t)s.in.n_props;
+        push(sg);
+        return;
+    }
+    const int order[7] = {OP_F, OP_U, OP_G, OP_X, OP_AND, OP_OR, OP_NOT};
+    const uint32_t bit[8] = {0, LTL_NOT, LTL_AND, LTL_OR, LTL_X, LTL_F, LTL_G, LTL_U};
+    for (int oi = 0; oi < 7; ++oi) {
+        const int op = order[oi];
+        if (!(s.in.ops & bit[op])) continue;
+        if (op == OP_F || op == OP_G || op == OP_X || op == OP_NOT) {
+            const uint64_t cnt = s.lvl_count[k - 1];
+            if (!cnt) continue;
+            Seg sg{};
+            sg.op = op; sg.kind = SEG_UNARY; sg.a_begin = s.lvl_begin[k - 1]; sg.a_count = cnt;
+            push(sg);
+            continue;
+        }
+        for (int cl = 1; cl <= k - 2; ++cl) {
+            const int cr = k - 1 - cl;
+            if (op != OP_U && cl > cr) continue;
+            const uint64_t na = s.lvl_count[cl], nb = s.lvl_count[cr];
+            if (!na || !nb) continue;
+            Seg sg{};
+            sg.op = op; sg.a_begin = s.lvl_begin[cl]; sg.a_count = na; sg.b_begin = s.lvl_begin[cr]; sg.b_count = nb;
+            if (op != OP_U && cl == cr) {
+                if (na < 2) continue;
+                sg.kind = SEG_TRI;
+            } else {
+                sg.kind = SEG_RECT;
+            }
+            push(sg);
+        }
+    }
+}
+
+}  // namespace
+
+// ===================================================================== Engine
+
+class Engine {
+public:
+    ltl_opts opts{};
+    int device = 0, n_sm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    int max_slots = 1;
+    bool keep_finished = false;   // contexts keep the last problem for introspection
+    // shared region at the start of the workspace
+    size_t o_probs = 0, o_ctrls = 0, o_segs = 0, o_counters = 0, o_jobs = 0, o_tokens = 0, o_ntok = 0, shared_end = 0;
+    size_t max_segs = 0;
+    Problem *h_probs = nullptr;
+    Ctrl *h_ctrls = nullptr;
+    Seg *h_segs = nullptr;
+    WalkJob *h_jobs = nullptr;
+    uint32_t *h_tokens = nullptr;
+    int *h_ntok = nullptr;
+    std::vector<Slot> slots;
+    FreeList mem;
+    struct Occ {
+        const void *fn;
+        int nt;
+        size_t smem;
+        int blocks;
+    };
+    std::vector<Occ> occ;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr, ev_op[kMaxGroups] = {};
+    uint64_t total_rounds = 0;
+
+    ~Engine() { teardown(); }
+
+    ltl_status setup(const ltl_opts *o, int max_resident, bool keep) {
+        opts = *o;
+        keep_finished = keep;
+        max_slots = std::max(1, std::min(max_resident, 4096));
+        cudaError_t e = cudaGetDevice(&device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(LTL_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+        }
+        if (opts.stream) stream = (cudaStream_t)opts.stream;
+        else {
+            LTL_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        // shared region
+        max_segs = (size_t)max_slots * 64 + 1024;
+        size_t cur = 0;
+        auto take = [&](size_t bytes) {
+            const size_t r = cur;
+            cur = round_up(cur + bytes, 256);
+            return r;
+        };
+        o_probs = take(sizeof(Problem) * max_slots);
+        o_ctrls = take(sizeof(Ctrl) * max_slots);
+        o_segs = take(sizeof(Seg) * max_segs);
+        o_counters = take(sizeof(unsigned long long) * kMaxGroups);
+        o_jobs = take(sizeof(WalkJob) * max_slots);
+        o_tokens = take(sizeof(uint32_t) * kMaxTokens * max_slots);
+        o_ntok = take(sizeof(int) * max_slots);
+        shared_end = cur;
+        LTL_CUDA_TRY(cudaMallocHost(&h_probs, sizeof(Problem) * max_slots));
+        LTL_CUDA_TRY(cudaMallocHost(&h_ctrls, sizeof(Ctrl) * max_slots));
+        LTL_CUDA_TRY(cudaMallocHost(&h_segs, sizeof(Seg) * max_segs));
+        LTL_CUDA_TRY(cudaMallocHost(&h_jobs, sizeof(WalkJob) * max_slots));
+        LTL_CUDA_TRY(cudaMallocHost(&h_tokens, sizeof(uint32_t) * kMaxTokens * max_slots));
+        LTL_CUDA_TRY(cudaMallocHost(&h_ntok, sizeof(int) * max_slots));
+        LTL_CUDA_TRY(cudaEventCreate(&ev_begin));
+        LTL_CUDA_TRY(cudaEventCreate(&ev_end));
+        for (int i = 0; i < kMaxGroups; ++i) LTL_CUDA_TRY(cudaEventCreate(&ev_op[i]));
+        slots.resize(max_slots);
+        if (opts.workspace) {
+            if (((uintptr_t)opts.workspace & 255u) != 0) return fail(LTL_ERR_INVALID, "workspace must be 256-byte aligned");
+            ws = (char *)opts.workspace;
+            ws_bytes = opts.workspace_bytes;
+            if (ws_bytes <= shared_end) return fail(LTL_ERR_OOM, "workspace too small");
+            mem.reset(shared_end, ws_bytes);
+        }
+        return LTL_OK;
+    }
+
+    void teardown() {
+        if (stream) cudaStreamSynchronize(stream);
+        if (ws_owned && ws) {
+            if (opts.free) opts.free(ws, stream, opts.user);
+            else cudaFree(ws);
+        }
+        ws = nullptr;
+        if (h_probs) cudaFreeHost(h_probs);
+        if (h_ctrls) cudaFreeHost(h_ctrls);
+        if (h_segs) cudaFreeHost(h_segs);
+        if (h_jobs) cudaFreeHost(h_jobs);
+        if (h_tokens) cudaFreeHost(h_tokens);
+        if (h_ntok) cudaFreeHost(h_ntok);
+        h_probs = nullptr; h_ctrls = nullptr; h_segs = nullptr; h_jobs = nullptr; h_tokens = nullptr; h_ntok = nullptr;
+        if (ev_begin) cudaEventDestroy(ev_begin);
+        if (ev_end) cudaEventDestroy(ev_end);
+        ev_begin = ev_end = nullptr;
+        for (int i = 0; i < kMaxGroups; ++i)
+            if (ev_op[i]) {
+                cudaEventDestroy(ev_op[i]);
+                ev_op[i] = nullptr;
+            }
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+        (void)cudaGetLastError();
+    }
+
+    // Without a caller workspace the engine allocates one (allocator callback
+    // or cudaMalloc): `need` bytes, or 40% of the free device memory.
+    ltl_status ensure_workspace(size_t need) {
+        if (ws && ws_bytes >= need) return LTL_OK;
+        if (opts.workspace) return fail(LTL_ERR_OOM, "workspace of %zu bytes too small (need %zu)", ws_bytes, need);
+        size_t want = need;
+        if (!opts.mem_budget_bytes) {
+            size_t fr = 0, tot = 0;
+            LTL_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+            want = std::max(need, (size_t)(0.4 * (double)(fr + (ws_owned ? ws_bytes : 0))));
+        }
+        if (ws_owned && ws) {
+            LTL_CUDA_TRY(cudaStreamSynchronize(stream));
+            if (opts.free) opts.free(ws, stream, opts.user);
+            else cudaFree(ws);
+            ws = nullptr;
+            ws_bytes = 0;
+        }
+        void *p = nullptr;
+        if (opts.alloc) {
+            p = opts.alloc(want, stream, opts.user);
+            if (!p) return fail(LTL_ERR_OOM, "allocator callback returned NULL for %zu bytes", want);
+        } else {
+            cudaError_t e = cudaMalloc(&p, want);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(LTL_ERR_OOM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+            }
+        }
+        ws = (char *)p;
+        ws_bytes = want;
+        ws_owned = true;
+        mem.reset(shared_end, ws_bytes);
+        for (auto &s : slots) s.state = SLOT_FREE;
+        return LTL_OK;
+    }
+
+    int resident() const {
+        int n = 0;
+        for (const auto &s : slots) n += s.state == SLOT_RUNNING;
+        return n;
+    }
+
+    const void *kernel_for(const Layout &L, int op) const {
+        if (L.narrow) return fused_kernel_ptr_narrow(L.C, op);
+        return L.G == 1 ? fused_kernel_ptr(L.Wt, L.C, op) : stream_kernel_ptr(L.Wt, L.C);
+    }
+
+    // Resident CTAs per SM of a kernel at a block size and dynamic shared
+    // memory (opted in); cached.
+    ltl_status occupancy(const void *fn, int nt, size_t smem, int &blocks) {
+        if (!fn) return fail(LTL_ERR_INVALID, "no level kernel for this shape");
+        for (const auto &e : occ)
+            if (e.fn == fn && e.nt == nt && e.smem == smem) {
+                blocks = e.blocks;
+                return LTL_OK;
+            }
+        if (smem > 0) LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int b = 0;
+        LTL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, nt, smem));
+        if (b < 1) return fail(LTL_ERR_INVALID, "level kernel cannot be resident (threads %d, smem %zu)", nt, smem);
+        occ.push_back({fn, nt, smem, b});
+        blocks = b;
+        return LTL_OK;
+    }
+
+    // Admits a problem into slot `si`: plans its layout for its budget (0: all
+    // of the largest free block), takes its memory, uploads and packs its
+    // traces.  Returns LTL_OK, or LTL_ERR_OOM when it does not fit right now.
+    // `in` is moved into the slot only when the admission succeeds.
+    ltl_status admit(int si, ProblemIn &in, uint64_t default_budget) {
+        Slot &s = slots[si];
+        Layout L;
+        const uint64_t budget = in.budget ? in.budget : default_budget;
+        const size_t avail = mem.largest();
+        ltl_status st = plan_layout(in, opts.max_chunks, budget, avail, L);
+        if (st != LTL_OK) return st;
+        size_t off = 0;
+        if (!mem.alloc(L.end, off)) return fail(LTL_ERR_OOM, "no free device region of %zu bytes", L.end);
+        s = Slot{};
+        s.in = std::move(in);
+        in = ProblemIn{};
+        s.L = L;
+        s.off = off;
+        s.bytes = L.end;
+        s.state = SLOT_RUNNING;
+        s.t_admit = wall_ms();
+        memset(&s.st, 0, sizeof s.st);
+        char *base = ws + off;
+        Ctrl *d_ctrl = (Ctrl *)(ws + o_ctrls) + si;
+        const uint64_t T = L.n_traces;
+        const uint32_t *d_letters = s.in.d_letters;
+        const uint64_t *d_offsets = s.in.d_offsets;
+        if (!s.in.device_input) {
+            uint32_t *dl = (uint32_t *)(base + L.o_letters);
+            uint64_t *dof = (uint64_t *)(base + L.o_offsets);
+            const uint64_t np = s.in.ho[0][s.in.hn[0]], nn = s.in.ho[1][s.in.hn[1]];
+            std::vector<uint64_t> offv(T + 1);
+            for (uint64_t i = 0; i <= s.in.hn[0]; ++i) offv[i] = s.in.ho[0][i];
+            for (uint64_t i = 1; i <= s.in.hn[1]; ++i) offv[s.in.hn[0] + i] = np + s.in.ho[1][i];
+            if (np) LTL_CUDA_TRY(cudaMemcpyAsync(dl, s.in.hl[0], 4 * np, cudaMemcpyHostToDevice, stream));
+            if (nn) LTL_CUDA_TRY(cudaMemcpyAsync(dl + np, s.in.hl[1], 4 * nn, cudaMemcpyHostToDevice, stream));
+            LTL_CUDA_TRY(cudaMemcpyAsync(dof, offv.data(), 8 * (T + 1), cudaMemcpyHostToDevice, stream));
+            s.st.h2d_bytes += 4 * (np + nn) + 8 * (T + 1);
+            LTL_CUDA_TRY(cudaStreamSynchronize(stream));   // offv is pageable and local
+            d_letters = dl;
+            d_offsets = dof;
+        }
+        uint64_t *d_mask = (uint64_t *)(base + L.o_mask);
+        uint64_t *d_keys = (uint64_t *)(base + L.o_keys);
+        uint64_t *d_atoms = (uint64_t *)(base + L.o_atoms);
+        LTL_CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
+        LTL_CUDA_TRY(cudaMemsetAsync(base + L.o_hkeys, 0, 8 * L.hslots, stream));
+        LTL_CUDA_TRY(cudaMemsetAsync(base + L.o_hvals, 0xff, 4 * L.hslots, stream));
+        LTL_CUDA_TRY(cudaMemsetAsync(d_mask, 0, 8 * L.stride, stream));
+        LTL_CUDA_TRY(cudaMemsetAsync(d_atoms, 0, 8 * L.stride * (uint64_t)L.n_props, stream));
+        if (L.narrow)
+            LTL_CUDA_TRY(launch_pack_narrow(d_letters, d_offsets, (uint32_t)T, L.plane, L.n_props, d_mask, d_atoms,
+                                            L.stride, d_ctrl, stream));
+        else
+            LTL_CUDA_TRY(launch_pack(d_letters, d_offsets, (uint32_t)T, L.plane, L.W, L.n_props, d_mask, d_atoms,
+                                     L.stride, d_ctrl, stream));
+        LTL_CUDA_TRY(launch_keys(d_keys, L.stride, kKeySeed, stream));
+        s.st.launches += 2;
+        Problem &pb = h_probs[si];
+        pb = Problem{};
+        pb.arena = (uint64_t *)(base + L.o_arena);
+        pb.stride = L.stride;
+        pb.plane = L.plane;
+        pb.mask = d_mask;
+        pb.keys = d_keys;
+        pb.atoms = d_atoms;
+        pb.prov = (uint64_t *)(base + L.o_prov);
+        pb.hkeys = (unsigned long long *)(base + L.o_hkeys);
+        pb.hvals = (uint32_t *)(base + L.o_hvals);
+        pb.hmask = L.hslots - 1;
+        pb.max_entries = L.max_entries;
+        pb.ctrl = d_ctrl;
+        pb.n_traces = (uint32_t)T;
+        pb.n_pos = L.n_pos;
+        pb.nsteps = L.nsteps;
+        pb.stop_first = opts.stop_on_solution == LTL_STOP_FIRST ? 1 : 0;
+        pb.groups = L.G;
+        pb.spin_limit = opts.spin_limit ? opts.spin_limit : (1ull << 20);
+        LTL_CUDA_TRY(cudaMemcpyAsync((Problem *)(ws + o_probs) + si, &h_probs[si], sizeof(Problem),
+                                     cudaMemcpyHostToDevice, stream));
+        s.st.n_traces = T;
+        s.st.words_per_trace = (uint32_t)L.W;
+        s.st.threads_per_cta = (uint32_t)L.NT;
+        s.st.traces_per_thread = (uint32_t)(L.narrow ? 4 * L.C : 2 * L.C);
+        s.st.traces_per_word = L.narrow ? 2u : 1u;
+        s.st.chunk_groups = L.G;
+        s.st.batch = (uint32_t)L.NB;
+        s.st.max_entries = L.max_entries;
+        int bps = 0;
+        if (occupancy(kernel_for(L, OP_U), L.NT, L.smem, bps) == LTL_OK) s.st.ctas_per_sm = (uint32_t)bps;
+        return LTL_OK;
+    }
+
+    void release(int si) {
+        Slot &s = slots[si];
+        if (s.bytes) mem.release(s.off, s.bytes);
+        s.bytes = 0;
+        s.state = SLOT_FREE;
+    }
+
+    // Marks a slot finished with `status` (formula rebuilt later if found).
+    void finish(Slot &s, ltl_status status) {
+        s.state = SLOT_DONE;
+        s.status = status;
+        s.t_done = wall_ms();
+    }
+
+    // One round: the next size level of every running problem.
+    ltl_status round() {
+        std::vector<Seg> segs;
+        std::vector<int> ran;   // slots that enumerate a level this round
+        for (int si = 0; si < max_slots; ++si) {
+            Slot &s = slots[si];
+            while (s.state == SLOT_RUNNING) {
+                const int k = s.level;
+                s.lvl_begin[k] = s.prev_entries;
+                const size_t before = segs.size();
+                level_segments(s, k, si, segs);
+                if (segs.size() > before) {
+                    ran.push_back(si);
+                    break;
+                }
+                // no candidate of this size (no connective allowed): an empty level
+                s.lvl_count[k] = 0;
+                s.st.levels_done = k;
+                if (++s.level > s.in.max_size) finish(s, LTL_NOT_FOUND);
+            }
+        }
+        if (ran.empty()) return LTL_OK;
+        if (segs.size() > max_segs) return fail(LTL_ERR_INVALID, "too many segments in one round");
+        // group by launch (kernel, block size); a group's shared memory is the
+        // largest any of its problems needs
+        struct Group {
+            const void *fn;
+            int nt, op, nb;
+            size_t smem;
+            std::vector<int> seg_ids;
+        };
+        std::vector<Group> groups;
+        for (int i = 0; i < (int)segs.size(); ++i) {
+            const Slot &s = slots[segs[i].prob];
+            const void *fn = kernel_for(s.L, segs[i].op);
+            int g = -1;
+            for (int j = 0; j < (int)groups.size(); ++j)
+                if (groups[j].fn == fn && groups[j].nt == s.L.NT) g = j;
+            if (g < 0) {
+                groups.push_back(Group{fn, s.L.NT, segs[i].op, s.L.NB, 0, {}});
+                g = (int)groups.size() - 1;
+            }
+            groups[g].smem = std::max(groups[g].smem, s.L.smem);
+            groups[g].seg_ids.push_back(i);
+        }
+        if ((int)groups.size() > kMaxGroups) return fail(LTL_ERR_INVALID, "too many launches in one round");
+        // tiles: about four per resident CTA in every launch
+        size_t n_out = 0;
+        std::vector<size_t> first(groups.size());
+        std::vector<uint64_t> tiles(groups.size());
+        std::vector<int> grid(groups.size());
+        for (size_t g = 0; g < groups.size(); ++g) {
+            Group &gr = groups[g];
+            int bps = 0;
+            ltl_status st = occupancy(gr.fn, gr.nt, gr.smem, bps);
+            if (st != LTL_OK) return st;
+            const uint64_t cap = (uint64_t)bps * (uint64_t)n_sm;
+            uint64_t cands = 0;
+            for (int i : gr.seg_ids) cands += seg_candidates(segs[i]);
+            const uint32_t cpt = tile_target(cands, cap, gr.nb);
+            uint64_t total = 0;
+            first[g] = n_out;
+            for (int i : gr.seg_ids) {
+                Seg sg = segs[i];
+                set_tiles(sg, cpt);
+                sg.tile_begin = total;
+                total += sg.n_tiles;
+                h_segs[n_out++] = sg;
+            }
+            tiles[g] = total;
+            grid[g] = (int)std::min<uint64_t>(total, cap);
+        }
+        Seg *d_segs = (Seg *)(ws + o_segs);
+        unsigned long long *d_counters = (unsigned long long *)(ws + o_counters);
+        LTL_CUDA_TRY(cudaMemcpyAsync(d_segs, h_segs, sizeof(Seg) * n_out, cudaMemcpyHostToDevice, stream));
+        LTL_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * groups.size(), stream));
+        LTL_CUDA_TRY(cudaEventRecord(ev_begin, stream));
+        for (size_t g = 0; g < groups.size(); ++g) {
+            LevelArgs la{};
+            la.segs = d_segs + first[g];
+            la.probs = (const Problem *)(ws + o_probs);
+            la.tile_counter = d_counters + g;
+            la.n_segs = (int)groups[g].seg_ids.size();
+            la.total_tiles = tiles[g];
+            void *args[] = {&la};
+            if (grid[g] > 0)
+                LTL_CUDA_TRY(cudaLaunchKernel(groups[g].fn, dim3(grid[g]), dim3(groups[g].nt), args, groups[g].smem,
+                                              stream));
+            LTL_CUDA_TRY(cudaEventRecord(ev_op[g], stream));
+        }
+        int hi = 0;
+        for (int si : ran) hi = std::max(hi, si + 1);
+        LTL_CUDA_TRY(cudaMemcpyAsync(h_ctrls, ws + o_ctrls, sizeof(Ctrl) * hi, cudaMemcpyDeviceToHost, stream));
+        LTL_CUDA_TRY(cudaStreamSynchronize(stream));
+        ++total_rounds;
+        float round_ms = 0.f;
+        LTL_CUDA_TRY(cudaEventElapsedTime(&round_ms, ev_begin, ev_op[groups.size() - 1]));
+        std::vector<float> op_ms(groups.size());
+        for (size_t g = 0; g < groups.size(); ++g) {
+            float t = 0.f;
+            LTL_CUDA_TRY(cudaEventElapsedTime(&t, g == 0 ? ev_begin : ev_op[g - 1], ev_op[g]));
+            op_ms[g] = t;
+        }
+        // close the level of every problem that ran
+        std::vector<int> found_slots;
+        for (int si : ran) {
+            Slot &s = slots[si];
+            const Ctrl &h = h_ctrls[si];
+            const int k = s.level;
+            s.rounds++;
+            s.st.ms[k] = round_ms;
+            for (size_t g = 0; g < groups.size(); ++g)
+                for (int i : groups[g].seg_ids)
+                    if (segs[i].prob == si) {
+                        s.st.op_ms[k][groups[g].op] = op_ms[g];
+                        break;
+                    }
+            s.st.d2h_bytes += sizeof(Ctrl);
+            if (h.invalid_letter) {
+                s.error = "trace letters use propositions >= n_props, offsets decrease, or a trace exceeds max_len";
+                finish(s, LTL_ERR_INVALID);
+                continue;
+            }
+            if (h.err) {
+                s.error = h.err == LTL_ERR_INVALID ? "launch shape / shared memory mismatch"
+                                                   : "device wait exceeded spin_limit";
+                finish(s, (ltl_status)h.err);
+                continue;
+            }
+            const uint64_t ent = std::min<uint64_t>(h.n_entries, s.L.max_entries);
+            s.lvl_count[k] = ent - s.prev_entries;
+            s.st.unique[k] = ent - s.prev_entries;
+            s.st.candidates[k] = h.cands - s.prev_cands;
+            s.prev_entries = ent;
+            s.prev_cands = h.cands;
+            s.st.entries = ent;
+            const bool stopped_early = (h.stop != 0) || h.cap_hit;
+            if (!stopped_early) s.st.levels_done = k;
+            if (h.found_count > 0) s.found = true;
+            if (h.cap_hit) {
+                if (s.found) found_slots.push_back(si);
+                finish(s, s.found ? LTL_OK : LTL_CAP_REACHED);
+                continue;
+            }
+            if (s.found && opts.stop_on_solution != LTL_STOP_NONE) {
+                found_slots.push_back(si);
+                finish(s, LTL_OK);
+                continue;
+            }
+            if (++s.level > s.in.max_size) {
+                if (s.found) found_slots.push_back(si);
+                finish(s, s.found ? LTL_OK : LTL_NOT_FOUND);
+            }
+        }
+        // one launch per group was shared by its problems: count it once each
+        for (size_t g = 0; g < groups.size(); ++g) {
+            std::vector<int> seen;
+            for (int i : groups[g].seg_ids) {
+                const int p = segs[i].prob;
+                if (std::find(seen.begin(), seen.end(), p) == seen.end()) {
+                    seen.push_back(p);
+                    slots[p].st.launches += 1;
+                }
+            }
+        }
+        return rebuild_formulas(found_slots);
+    }
+
+    // One provenance walk for every problem that found a separator.
+    ltl_status rebuild_formulas(const std::vector<int> &found_slots) {
+        if (found_slots.empty()) return LTL_OK;
+        const int n = (int)found_slots.size();
+        for (int j = 0; j < n; ++j) {
+            const int si = found_slots[j];
+            const Slot &s = slots[si];
+            h_jobs[j].prov = (const uint64_t *)(ws + s.off + s.L.o_prov);
+            h_jobs[j].n_entries = s.prev_entries;
+            h_jobs[j].root = h_ctrls[si].found_prov;
+        }
+        WalkJob *d_jobs = (WalkJob *)(ws + o_jobs);
+        uint32_t *d_tokens = (uint32_t *)(ws + o_tokens);
+        int *d_ntok = (int *)(ws + o_ntok);
+        LTL_CUDA_TRY(cudaMemcpyAsync(d_jobs, h_jobs, sizeof(WalkJob) * n, cudaMemcpyHostToDevice, stream));
+        LTL_CUDA_TRY(launch_walk_batch(d_jobs, n, d_tokens, kMaxTokens, d_ntok, stream));
+        LTL_CUDA_TRY(cudaMemcpyAsync(h_tokens, d_tokens, sizeof(uint32_t) * kMaxTokens * n, cudaMemcpyDeviceToHost,
+                                     stream));
+        LTL_CUDA_TRY(cudaMemcpyAsync(h_ntok, d_ntok, sizeof(int) * n, cudaMemcpyDeviceToHost, stream));
+        LTL_CUDA_TRY(cudaStreamSynchronize(stream));
+        for (int j = 0; j < n; ++j) {
+            Slot &s = slots[found_slots[j]];
+            s.st.launches += 1;
+            s.st.d2h_bytes += sizeof(uint32_t) * kMaxTokens + sizeof(int);
+            if (h_ntok[j] <= 0) {
+                s.status = LTL_ERR_CUDA;
+                s.error = "provenance walk failed";
+                continue;
+            }
+            s.formula.clear();
+            tokens_to_text(h_tokens + (size_t)j * kMaxTokens, h_ntok[j], 0, s.formula);
+            s.st.found_size = h_ctrls[found_slots[j]].found_level;
+        }
+        return LTL_OK;
+    }
+
+    // Formula text of cache entry idx of slot si (for introspection).
+    ltl_status entry_formula(int si, uint64_t idx, std::string &text) {
+        const Slot &s = slots[si];
+        uint64_t p = 0;
+        LTL_CUDA_TRY(cudaMemcpyAsync(&h_jobs[0].root, ws + s.off + s.L.o_prov + 8 * idx, 8, cudaMemcpyDeviceToHost,
+                                     stream));
+        LTL_CUDA_TRY(cudaStreamSynchronize(stream));
+        p = h_jobs[0].root;
+        h_jobs[0].prov = (const uint64_t *)(ws + s.off + s.L.o_prov);
+        h_jobs[0].n_entries = s.prev_entries;
+        h_jobs[0].root = p;
+        WalkJob *d_jobs = (WalkJob *)(ws + o_jobs);
+        LTL_CUDA_TRY(cudaMemcpyAsync(d_jobs, h_jobs, sizeof(WalkJob), cudaMemcpyHostToDevice, stream));
+        LTL_CUDA_TRY(launch_walk_batch(d_jobs, 1, (uint32_t *)(ws + o_tokens), kMaxTokens, (int *)(ws + o_ntok), stream));
+        LTL_CUDA_TRY(cudaMemcpyAsync(h_tokens, ws + o_tokens, sizeof(uint32_t) * kMaxTokens, cudaMemcpyDeviceToHost,
+                                     stream));
+        LTL_CUDA_TRY(cudaMemcpyAsync(h_ntok, ws + o_ntok, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        LTL_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (h_ntok[0] <= 0) return fail(LTL_ERR_CUDA, "provenance walk failed");
+        text.clear();
+        tokens_to_text(h_tokens, h_ntok[0], 0, text);
+        return LTL_OK;
+    }
+
+    void fill_result(const Slot &s, ltl_result &r) const {
+        memset(&r, 0, sizeof r);
+        r.id = s.in.id;
+        r.status = s.status;
+        r.found_size = s.status == LTL_OK ? s.st.found_size : 0;
+        r.levels_done = s.st.levels_done;
+        snprintf(r.formula, sizeof r.formula, "%s", s.status == LTL_OK ? s.formula.c_str() : "");
+        for (int k = 0; k < kMaxLevels; ++k) {
+            r.unique[k] = s.st.unique[k];
+            r.candidates[k] = s.st.candidates[k];
+        }
+        r.n_traces = s.st.n_traces;
+        r.rounds = s.rounds;
+        r.queue_ms = s.t_admit - s.in.t_submit;
+        r.latency_ms = s.t_done - s.in.t_submit;
+    }
+};
+
+// Builds the ProblemIn of host traces (copying them when `own`).
+ltl_status problem_from_host(const ltl_traces *P, const ltl_traces *N, int n_props, uint32_t ops, int max_size,
+                             uint64_t budget, bool own, ProblemIn &in) {
+    ltl_status s = check_common(n_props, ops, max_size);
+    if (s != LTL_OK) return s;
+    if ((s = check_traces(P, "P")) != LTL_OK) return s;
+    if ((s = check_traces(N, "N")) != LTL_OK) return s;
+    const ltl_traces *tr[2] = {P, N};
+    for (int h = 0; h < 2; ++h) {
+        in.hn[h] = tr[h]->n_traces;
+        if (own) {
+            const uint64_t np = tr[h]->offsets[tr[h]->n_traces];
+            in.own_l[h].assign(tr[h]->letters, tr[h]->letters + np);
+            in.own_o[h].assign(tr[h]->offsets, tr[h]->offsets + tr[h]->n_traces + 1);
+            if (in.own_l[h].empty()) in.own_l[h].push_back(0);
+            in.hl[h] = in.own_l[h].data();
+            in.ho[h] = in.own_o[h].data();
+        } else {
+            in.hl[h] = tr[h]->letters;
+            in.ho[h] = tr[h]->offsets;
+        }
+    }
+    in.n_pos = P->n_traces;
+    in.n_neg = N->n_traces;
+    in.max_len = std::max(traces_max_len(P), traces_max_len(N));
+    in.total_pos = P->offsets[P->n_traces] + N->offsets[N->n_traces];
+    in.n_props = n_props;
+    in.ops = ops;
+    in.max_size = max_size;
+    in.budget = budget;
+    in.t_submit = wall_ms();
+    return LTL_OK;
+}
+
+ltl_opts default_opts() {
+    ltl_opts o;
+    memset(&o, 0, sizeof o);
+    o.stop_on_solution = LTL_STOP_FIRST;
+    return o;
+}
+
+// Runs one problem to completion in slot 0 of engine e (the whole workspace).
+ltl_status run_single(Engine &e, ProblemIn &&in, char *formula_out, size_t formula_cap, ltl_stats *stats) {
+    const double t0 = wall_ms();
+    if (formula_out && formula_cap) formula_out[0] = '\0';
+    // the previous problem of a context is kept until the next call
+    if (e.slots[0].state != SLOT_FREE) e.release(0);
+    // size the workspace for this problem's fixed part (and let it grow)
+    Layout probe;
+    ltl_status s = plan_layout(in, e.opts.max_chunks, 0, (uint64_t)1 << 62, probe);
+    if (s != LTL_OK) return s;
+    const size_t fixed = probe.o_hkeys + (1 << 20);
+    s = e.ensure_workspace(e.shared_end + fixed + (e.opts.mem_budget_bytes ? e.opts.mem_budget_bytes : 0));
+    if (s != LTL_OK) return s;
+    uint64_t budget = e.opts.mem_budget_bytes;
+    if (e.opts.workspace && e.opts.mem_budget_bytes) budget = std::min<uint64_t>(budget, e.mem.largest());
+    s = e.admit(0, in, budget);
+    if (s != LTL_OK) return s;
+    while (e.slots[0].state == SLOT_RUNNING) {
+        s = e.round();
+        if (s != LTL_OK) return s;
+    }
+    Slot &sl = e.slots[0];
+    sl.st.total_ms = wall_ms() - t0;
+    if (stats) *stats = sl.st;
+    if (sl.status < 0) return fail(sl.status, "%s", sl.error.c_str());
+    if (sl.status == LTL_OK) {
+        s = write_formula(sl.formula, formula_out, formula_cap);
+        if (s != LTL_OK) return s;
+    }
+    return sl.status;
+}
+
+}  // namespace ltl
+
+using namespace ltl;
+
+// ==================================================================== C ABI
+
+struct ltl_ctx {
+    Engine e;
+};
+
+struct ltl_server {
+    Engine e;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ProblemIn> queue;
+    std::deque<ltl_result> done;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_id = 0;
+    uint64_t default_budget = 0;
+    ltl_status worker_error = LTL_OK;
+    std::string worker_msg;
+};
+
+extern "C" {
+
+ltl_status ltl_ctx_create(const ltl_opts *opts, ltl_ctx **out) {
+    if (!out) return fail(LTL_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    const ltl_opts o = opts ? *opts : default_opts();
+    if (o.stop_on_solution < 0 || o.stop_on_solution > 2) return fail(LTL_ERR_INVALID, "stop_on_solution must be 0, 1 or 2");
+    ltl_ctx *c = new ltl_ctx();
+    ltl_status s = c->e.setup(&o, 1, true);
+    if (s != LTL_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return LTL_OK;
+}
+
+void ltl_ctx_destroy(ltl_ctx *c) { delete c; }
+
+ltl_status ltl_ctx_learn(ltl_ctx *c, const ltl_traces *P, const ltl_traces *N, int n_props, uint32_t ops,
+                         int max_size, char *formula_out, size_t formula_cap, ltl_stats *stats) {
+    if (!c) return fail(LTL_ERR_INVALID, "ctx is NULL");
+    ProblemIn in;
+    ltl_status s = problem_from_host(P, N, n_props, ops, max_size, 0, false, in);
+    if (s != LTL_OK) return s;
+    return run_single(c->e, std::move(in), formula_out, formula_cap, stats);
+}
+
+ltl_status ltl_ctx_learn_device(ltl_ctx *c, const uint32_t *d_letters, const uint64_t *d_offsets, uint64_t n_pos,
+                                uint64_t n_neg, uint32_t max_len, int n_props, uint32_t ops, int max_size,
+                                char *formula_out, size_t formula_cap, ltl_stats *stats) {
+    if (!c) return fail(LTL_ERR_INVALID, "ctx is NULL");
+    ltl_status s = check_common(n_props, ops, max_size);
+    if (s != LTL_OK) return s;
+    if (!d_offsets || (!d_letters && max_len > 0)) return fail(LTL_ERR_INVALID, "device trace buffers are NULL");
+    ProblemIn in;
+    in.device_input = true;
+    in.d_letters = d_letters;
+    in.d_offsets = d_offsets;
+    in.n_pos = n_pos;
+    in.n_neg = n_neg;
+    in.max_len = max_len;
+    in.n_props = n_props;
+    in.ops = ops;
+    in.max_size = max_size;
+    in.t_submit = wall_ms();
+    return run_single(c->e, std::move(in), formula_out, formula_cap, stats);
+}
+
+ltl_status ltl_learn(const ltl_traces *P, const ltl_traces *N, int n_props, uint32_t ops, int max_size,
+                     const ltl_opts *opts, char *formula_out, size_t formula_cap, ltl_stats *stats) {
+    ltl_ctx *c = nullptr;
+    ltl_status s = ltl_ctx_create(opts, &c);
+    if (s != LTL_OK) return s;
+    s = ltl_ctx_learn(c, P, N, n_props, ops, max_size, formula_out, formula_cap, stats);
+    ltl_ctx_destroy(c);
+    return s;
+}
+
+ltl_status ltl_ctx_level_range(ltl_ctx *c, int level, uint64_t *begin, uint64_t *count) {
+    if (!c || !begin || !count) return fail(LTL_ERR_INVALID, "NULL argument");
+    const Slot &s = c->e.slots[0];
+    if (s.state != SLOT_DONE) return fail(LTL_ERR_INVALID, "no learn result on this context");
+    if (level < 1 || level >= kMaxLevels) return fail(LTL_ERR_INVALID, "level out of range");
+    *begin = s.lvl_begin[level];
+    *count = s.lvl_count[level];
+    return LTL_OK;
+}
+
+ltl_status ltl_ctx_entry(ltl_ctx *c, uint64_t idx, char *formula_out, size_t formula_cap, uint64_t *cs_out,
+                         int words_per_trace) {
+    if (!c) return fail(LTL_ERR_INVALID, "ctx is NULL");
+    Engine &e = c->e;
+    const Slot &s = e.slots[0];
+    if (s.state != SLOT_DONE) return fail(LTL_ERR_INVALID, "no learn result on this context");
+    const Layout &L = s.L;
+    if (idx >= s.prev_entries) return fail(LTL_ERR_INVALID, "entry %llu out of range", (unsigned long long)idx);
+    if (formula_out) {
+        std::string text;
+        ltl_status st = e.entry_formula(0, idx, text);
+        if (st != LTL_OK) return st;
+        if ((st = write_formula(text, formula_out, formula_cap)) != LTL_OK) return st;
+    }
+    if (!cs_out) return LTL_OK;
+    const char *src = e.ws + s.off + L.o_arena + 8 * L.stride * idx;
+    if (L.narrow) {
+        if (words_per_trace != 1) return fail(LTL_ERR_INVALID, "words_per_trace must be 1");
+        // word q of the plane holds traces 2q (low half) and 2q + 1 (high half)
+        const uint64_t nw = ((uint64_t)L.n_traces + 1) / 2;
+        std::vector<uint64_t> words(nw ? nw : 1);
+        LTL_CUDA_TRY(cudaMemcpyAsync(words.data(), src, 8 * nw, cudaMemcpyDeviceToHost, e.stream));
+        LTL_CUDA_TRY(cudaStreamSynchronize(e.stream));
+        for (uint64_t t = 0; t < L.n_traces; ++t) cs_out[t] = (words[t / 2] >> (32 * (t & 1))) & 0xffffffffull;
+        return LTL_OK;
+    }
+    if (words_per_trace != L.W) return fail(LTL_ERR_INVALID, "words_per_trace must be %d", L.W);
+    // plane w of the entry holds word w of every trace: a strided 2-D copy
+    for (int w = 0; w < L.W; ++w)
+        LTL_CUDA_TRY(cudaMemcpy2DAsync(cs_out + w, 8 * (size_t)L.W, src + 8 * L.plane * w, 8, 8, (size_t)L.n_traces,
+                                       cudaMemcpyDeviceToHost, e.stream));
+    LTL_CUDA_TRY(cudaStreamSynchronize(e.stream));
+    return LTL_OK;
+}
+
+ltl_status ltl_learn_batch(int n, const ltl_problem *problems, const ltl_opts *opts, ltl_result *out) {
+    if (n < 0 || (n > 0 && (!problems || !out))) return fail(LTL_ERR_INVALID, "bad batch arguments");
+    if (n == 0) return LTL_OK;
+    const ltl_opts o = opts ? *opts : default_opts();
+    if (o.stop_on_solution < 0 || o.stop_on_solution > 2) return fail(LTL_ERR_INVALID, "stop_on_solution must be 0, 1 or 2");
+    const int resident_cap = std::min(n, 1024);
+    Engine e;
+    ltl_status s = e.setup(&o, resident_cap, false);
+    if (s != LTL_OK) return s;
+    // problems are queued in input order; each needs its budget (or an equal
+    // share of the workspace) of contiguous memory to be admitted
+    std::deque<int> queue;
+    std::vector<ProblemIn> ins(n);
+    for (int i = 0; i < n; ++i) {
+        const ltl_problem &p = problems[i];
+        s = problem_from_host(&p.P, &p.N, p.n_props, p.ops, p.max_size, p.mem_budget_bytes, false, ins[i]);
+        memset(&out[i], 0, sizeof(ltl_result));
+        out[i].id = (uint64_t)i;
+        if (s != LTL_OK) {
+            out[i].status = s;
+            continue;
+        }
+        ins[i].id = (uint64_t)i;
+        queue.push_back(i);
+    }
+    s = e.ensure_workspace(e.shared_end + ((size_t)64 << 20));
+    if (s != LTL_OK) return s;
+    const uint64_t share = (e.ws_bytes - e.shared_end) / (uint64_t)std::max(1, std::min<int>(n, resident_cap));
+    while (!queue.empty() || e.resident() > 0) {
+        // admit in order while memory and slots allow
+        while (!queue.empty()) {
+            int si = -1;
+            for (int j = 0; j < e.max_slots; ++j)
+                if (e.slots[j].state == SLOT_FREE) {
+                    si = j;
+                    break;
+                }
+            if (si < 0) break;
+            const int pi = queue.front();
+            const uint64_t budget = ins[pi].budget ? ins[pi].budget : share;
+            ltl_status as = e.admit(si, ins[pi], budget);
+            if (as == LTL_OK) {
+                queue.pop_front();
+                continue;
+            }
+            if (as == LTL_ERR_OOM && e.resident() > 0) break;   // wait for memory
+            out[pi].status = as;   // does not fit even alone, or invalid
+            queue.pop_front();
+        }
+        if (e.resident() == 0) continue;
+        s = e.round();
+        if (s != LTL_OK) return s;
+        for (int j = 0; j < e.max_slots; ++j) {
+            Slot &sl = e.slots[j];
+            if (sl.state != SLOT_DONE) continue;
+            e.fill_result(sl, out[sl.in.id]);
+            e.release(j);
+        }
+    }
+    return LTL_OK;
+}
+
+static void server_loop(ltl_server *srv) {
+    cudaSetDevice(srv->e.device);
+    Engine &e = srv->e;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->cv_work.wait(lk, [&] { return srv->stop || !srv->queue.empty() || e.resident() > 0; });
+            if (srv->stop) return;
+            // admission between rounds: in arrival order, while memory fits
+            while (!srv->queue.empty()) {
+                int si = -1;
+                for (int j = 0; j < e.max_slots; ++j)
+                    if (e.slots[j].state == SLOT_FREE) {
+                        si = j;
+                        break;
+                    }
+                if (si < 0) break;
+                ProblemIn &front = srv->queue.front();
+                const uint64_t id = front.id;
+                const double t_sub = front.t_submit;
+                const uint64_t budget = front.budget ? front.budget : srv->default_budget;
+                ltl_status as = e.admit(si, front, budget);
+                if (as == LTL_OK) {
+                    srv->queue.pop_front();
+                    continue;
+                }
+                if (as == LTL_ERR_OOM && e.resident() > 0) break;   // wait for memory
+                ltl_result r;
+                memset(&r, 0, sizeof r);
+                r.id = id;
+                r.status = as;
+                r.latency_ms = wall_ms() - t_sub;
+                srv->queue.pop_front();
+                srv->done.push_back(r);
+                srv->cv_done.notify_all();
+            }
+        }
+        if (e.resident() == 0) continue;
+        ltl_status s = e.round();
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (s != LTL_OK) {
+            srv->worker_error = s;
+            srv->worker_msg = "round failed";
+            // fail every resident problem
+            for (int j = 0; j < e.max_slots; ++j)
+                if (e.slots[j].state == SLOT_RUNNING) e.finish(e.slots[j], s);
+        }
+        for (int j = 0; j < e.max_slots; ++j) {
+            Slot &sl = e.slots[j];
+            if (sl.state != SLOT_DONE) continue;
+            ltl_result r;
+            e.fill_result(sl, r);
+            srv->done.push_back(r);
+            e.release(j);
+        }
+        srv->cv_done.notify_all();
+    }
+}
+
+ltl_status ltl_server_create(const ltl_opts *opts, int max_resident, ltl_server **out) {
+    if (!out) return fail(LTL_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    const ltl_opts o = opts ? *opts : default_opts();
+    if (max_resident < 1 || max_resident > 4096) return fail(LTL_ERR_INVALID, "max_resident must be in 1..4096");
+    ltl_server *srv = new ltl_server();
+    ltl_status s = srv->e.setup(&o, max_resident, false);
+    if (s == LTL_OK) s = srv->e.ensure_workspace(srv->e.shared_end + ((size_t)64 << 20));
+    if (s != LTL_OK) {
+        delete srv;
+        return s;
+    }
+    srv->default_budget = (srv->e.ws_bytes - srv->e.shared_end) / (uint64_t)max_resident;
+    if (o.mem_budget_bytes) srv->default_budget = o.mem_budget_bytes;
+    srv->worker = std::thread(server_loop, srv);
+    *out = srv;
+    return LTL_OK;
+}
+
+ltl_status ltl_server_submit(ltl_server *srv, const ltl_problem *p, uint64_t *id) {
+    if (!srv || !p) return fail(LTL_ERR_INVALID, "NULL argument");
+    ProblemIn in;
+    ltl_status s = problem_from_host(&p->P, &p->N, p->n_props, p->ops, p->max_size, p->mem_budget_bytes, true, in);
+    if (s != LTL_OK) return s;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    in.id = srv->next_id++;
+    if (id) *id = in.id;
+    srv->queue.push_back(std::move(in));
+    srv->cv_work.notify_all();
+    return LTL_OK;
+}
+
+ltl_status ltl_server_poll(ltl_server *srv, ltl_result *out, int max, int *n_out, int wait_ms) {
+    if (!srv || !n_out || (max > 0 && !out)) return fail(LTL_ERR_INVALID, "NULL argument");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    if (srv->done.empty() && wait_ms > 0)
+        srv->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !srv->done.empty(); });
+    int n = 0;
+    while (n < max && !srv->done.empty()) {
+        out[n++] = srv->done.front();
+        srv->done.pop_front();
+    }
+    *n_out = n;
+    if (srv->worker_error != LTL_OK && n == 0) return fail(srv->worker_error, "%s", srv->worker_msg.c_str());
+    return LTL_OK;
+}
+
+ltl_status ltl_server_pending(ltl_server *srv, uint64_t *queued, uint64_t *resident) {
+    if (!srv) return fail(LTL_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (queued) *queued = srv->queue.size();
+    if (resident) *resident = (uint64_t)srv->e.resident();
+    return LTL_OK;
+}
+
+void ltl_server_destroy(ltl_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv_work.notify_all();
+    }
+    if (srv->worker.joinable()) srv->worker.join();
+    delete srv;
+}
+
+}  // extern "C"

@@ -317,10 +317,16 @@ __device__ __forceinline__ void decode_tile(const Seg &sg, uint64_t k, uint64_t 
     b1 = min(b0 + sg.tb, sg.b_count);
 }
 
+// The segment holding `tile`: the last one whose first tile is <= tile
+// (binary search; a launch may carry the segments of many problems).
 __device__ __forceinline__ int find_segment(const LevelArgs &la, unsigned long long tile) {
-    int si = 0;
-    while (si + 1 < la.n_segs && la.segs[si + 1].tile_begin <= tile) ++si;
-    return si;
+    int lo = 0, hi = la.n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (la.segs[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 }  // namespace lvl

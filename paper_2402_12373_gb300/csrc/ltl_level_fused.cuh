@@ -69,6 +69,7 @@ struct FusedShared {
     unsigned long long fp[32][NB];
     uint32_t bad[32];
     unsigned long long tile;
+    int skip;
     unsigned long long idx[2][NB];
     int dec[2][NB];
     uint32_t neq[2];
@@ -304,20 +305,10 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
 
 }  // namespace
 
-// Register cap: 168 for 8 words per thread (three 128-thread CTAs per SM),
-// 128 for smaller shapes (at most 256 threads per CTA either way).
-template <int W, int C, int NB, int OP, bool NARROW>
-__global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(Problem pb, LevelArgs la) {
-    extern __shared__ __align__(128) unsigned char dyn_smem[];
-    uint64_t *slots = reinterpret_cast<uint64_t *>(dyn_smem);
-    __shared__ FusedShared<NB> sh;
-    LaneConst lc;
-    lc.tid = threadIdx.x;
-    lc.lane = lc.tid & 31;
-    lc.warp = lc.tid >> 5;
-    lc.nwarps = blockDim.x >> 5;
-    lc.toff = 2ull * (uint64_t)lc.tid;
-    lc.cs = 2ull * (uint64_t)blockDim.x;
+// Per-problem lane constants: plane geometry and which of the thread's trace
+// slots are positive / real (for the soundness test of eq. (dagger)).
+template <int C, bool NARROW>
+__device__ __forceinline__ void set_lane_problem(const Problem &pb, LaneConst &lc) {
     lc.plane = pb.plane;
     lc.stride = pb.stride;
     lc.want = 0;
@@ -339,36 +330,63 @@ __global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(Problem
                 if (word < pb.n_traces) lc.care |= 1u << (2 * c + j);
             }
         }
-    // the operand slots must fit the dynamic shared memory this launch got
+}
+
+// Register cap: 168 for 8 words per thread (three 128-thread CTAs per SM),
+// 128 for smaller shapes (at most 256 threads per CTA either way).
+template <int W, int C, int NB, int OP, bool NARROW>
+__global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(LevelArgs la) {
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    uint64_t *slots = reinterpret_cast<uint64_t *>(dyn_smem);
+    __shared__ FusedShared<NB> sh;
+    LaneConst lc;
+    lc.tid = threadIdx.x;
+    lc.lane = lc.tid & 31;
+    lc.warp = lc.tid >> 5;
+    lc.nwarps = blockDim.x >> 5;
+    lc.toff = 2ull * (uint64_t)lc.tid;
+    lc.cs = 2ull * (uint64_t)blockDim.x;
+    // the operand slots of every problem in the launch must fit its dynamic
+    // shared memory (checked per tile below)
     uint32_t dsmem;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsmem));
-    if ((uint64_t)dsmem < (uint64_t)(NB + 1) * pb.stride * 8ull) {
-        if (lc.tid == 0) atomicCAS(&pb.ctrl->err, 0, -1 /* LTL_ERR_INVALID */);
-        return;
-    }
     if (lc.tid == 0) {
         mbar_init(&sh.bar, 1);
         sh.neq[0] = sh.neq[1] = 0u;
     }
     __syncthreads();
     uint32_t phase = 0, round = 0;
-    unsigned long long done = 0;
     for (;;) {
+        // thread 0 takes a tile and reads its problem's stop flag
         if (lc.tid == 0) {
-            unsigned long long t = ~0ull;
-            if (!ld_volatile_i32(&pb.ctrl->stop)) t = atomicAdd(&pb.ctrl->next_tile[la.counter], 1ull);
+            const unsigned long long t = atomicAdd(la.tile_counter, 1ull);
+            int skip = 1;
+            if (t < la.total_tiles) {
+                const int si = find_segment(la, t);
+                skip = ld_volatile_i32(&la.probs[la.segs[si].prob].ctrl->stop);
+            }
             sh.tile = t;
+            sh.skip = skip;
         }
         __syncthreads();
         const unsigned long long tile = sh.tile;
+        const int skip = sh.skip;
         __syncthreads();
         if (tile >= la.total_tiles) break;
+        if (skip) continue;
         const Seg sg = la.segs[find_segment(la, tile)];
+        const Problem pb = la.probs[sg.prob];
+        if ((uint64_t)dsmem < (uint64_t)(NB + 1) * pb.stride * 8ull) {   // slots must fit the launch's smem
+            if (lc.tid == 0) atomicCAS(&pb.ctrl->err, 0, -1 /* LTL_ERR_INVALID */);
+            continue;
+        }
+        set_lane_problem<C, NARROW>(pb, lc);
         uint64_t a0, a1, b0, b1;
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
-        fused_tile<W, C, NB, OP, NARROW>(pb, la.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done);
+        unsigned long long done = 0;
+        fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done);
+        if (lc.tid == 0 && done) atomicAdd(&pb.ctrl->cands, done);
     }
-    if (lc.tid == 0 && done) atomicAdd(&pb.ctrl->cands, done);
 }
 
 }  // namespace lvl

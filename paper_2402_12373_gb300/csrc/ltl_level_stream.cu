@@ -16,6 +16,7 @@ struct StreamShared {
     unsigned long long fp[32];
     int bad[32];
     unsigned long long tile;
+    int skip;
     unsigned long long idx;
     unsigned long long h;
     int dec;
@@ -155,26 +156,31 @@ __device__ __forceinline__ unsigned long long stream_tile(const Problem &pb, int
 }  // namespace
 
 template <int W, int C>
-__global__ void __launch_bounds__(256) stream_level_kernel(Problem pb, LevelArgs la) {
+__global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
     __shared__ StreamShared sh;
     const int tid = threadIdx.x, NT = blockDim.x;
-    unsigned long long done = 0;
     for (;;) {
         if (tid == 0) {
-            unsigned long long t = ~0ull;
-            if (!ld_volatile_i32(&pb.ctrl->stop)) t = atomicAdd(&pb.ctrl->next_tile[la.counter], 1ull);
+            const unsigned long long t = atomicAdd(la.tile_counter, 1ull);
+            int skip = 1;
+            if (t < la.total_tiles) skip = ld_volatile_i32(&la.probs[la.segs[find_segment(la, t)].prob].ctrl->stop);
             sh.tile = t;
+            sh.skip = skip;
         }
         __syncthreads();
         const unsigned long long tile = sh.tile;
+        const int skip = sh.skip;
         __syncthreads();
         if (tile >= la.total_tiles) break;
+        if (skip) continue;
         const Seg sg = la.segs[find_segment(la, tile)];
+        const Problem pb = la.probs[sg.prob];
         uint64_t a0, a1, b0, b1;
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
+        unsigned long long done = 0;
         switch (sg.op) {
 #define LTL_STREAM_CASE(OPV) \
-    case OPV: done += stream_tile<W, C, OPV>(pb, la.level, sg, a0, a1, b0, b1, sh, NT, tid); break;
+    case OPV: done = stream_tile<W, C, OPV>(pb, sg.level, sg, a0, a1, b0, b1, sh, NT, tid); break;
             LTL_STREAM_CASE(OP_ATOM)
             LTL_STREAM_CASE(OP_NOT)
             LTL_STREAM_CASE(OP_AND)
@@ -186,8 +192,8 @@ __global__ void __launch_bounds__(256) stream_level_kernel(Problem pb, LevelArgs
 #undef LTL_STREAM_CASE
         default: break;
         }
+        if (tid == 0 && done) atomicAdd(&pb.ctrl->cands, done);
     }
-    if (tid == 0 && done) atomicAdd(&pb.ctrl->cands, done);
 }
 
 }  // namespace lvl

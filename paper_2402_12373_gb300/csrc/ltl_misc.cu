@@ -100,30 +100,35 @@ __global__ void keys_kernel(uint64_t *keys, uint64_t n, uint64_t seed) {
 }
 
 // ---------------------------------------------------------------------------
-// Provenance walk: the syntax tree of a cache entry (or of the recorded
-// separator) as a pre-order token list, op | (atom index << 8).  One thread.
+// Provenance walk: the syntax tree of a cache entry (or of a recorded
+// separator) as a pre-order token list, op | (atom index << 8).  One thread
+// per job; job j writes tokens[j * cap ...] and its count to n_out[j] (-1 if
+// the provenance is inconsistent or the tree exceeds cap).
 // ---------------------------------------------------------------------------
-__global__ void walk_kernel(const uint64_t *prov, uint64_t n_entries, uint64_t root_prov, uint32_t *tokens,
-                            int cap, int *n_out) {
+__global__ void walk_batch_kernel(const WalkJob *jobs, int n_jobs, uint32_t *tokens, int cap, int *n_out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_jobs) return;
+    const WalkJob jb = jobs[j];
+    uint32_t *tok = tokens + (uint64_t)j * cap;
     uint64_t stack[2 * kMaxLevels + 2];
     int sp = 0, n = 0;
     bool ok = true;
-    stack[sp++] = root_prov;
+    stack[sp++] = jb.root;
     while (sp > 0 && n < cap && ok) {
         const uint64_t p = stack[--sp];
         const int op = prov_op(p);
         if (op > OP_U) { ok = false; break; }
-        tokens[n++] = (uint32_t)op | ((uint32_t)(op == OP_ATOM ? prov_a(p) : 0) << 8);
+        tok[n++] = (uint32_t)op | ((uint32_t)(op == OP_ATOM ? prov_a(p) : 0) << 8);
         if (op == OP_ATOM) continue;
         const bool binary = op == OP_AND || op == OP_OR || op == OP_U;
-        if (prov_a(p) >= n_entries || (binary && prov_b(p) >= n_entries) || sp + 2 > 2 * kMaxLevels + 2) {
+        if (prov_a(p) >= jb.n_entries || (binary && prov_b(p) >= jb.n_entries) || sp + 2 > 2 * kMaxLevels + 2) {
             ok = false;
             break;
         }
-        if (binary) stack[sp++] = prov[prov_b(p)];   // pushed first: visited after the left subtree
-        stack[sp++] = prov[prov_a(p)];
+        if (binary) stack[sp++] = jb.prov[prov_b(p)];   // pushed first: visited after the left subtree
+        stack[sp++] = jb.prov[prov_a(p)];
     }
-    *n_out = (ok && sp == 0) ? n : -1;
+    n_out[j] = (ok && sp == 0) ? n : -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -235,9 +240,10 @@ cudaError_t launch_keys(uint64_t *keys, uint64_t n, uint64_t seed, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk(const uint64_t *prov, uint64_t n_entries, uint64_t root_prov, uint32_t *tokens, int cap,
-                        int *n_out, cudaStream_t s) {
-    walk_kernel<<<1, 1, 0, s>>>(prov, n_entries, root_prov, tokens, cap, n_out);
+cudaError_t launch_walk_batch(const WalkJob *jobs, int n_jobs, uint32_t *tokens, int cap, int *n_out, cudaStream_t s) {
+    if (n_jobs <= 0) return cudaSuccess;
+    const int th = 64;
+    walk_batch_kernel<<<(n_jobs + th - 1) / th, th, 0, s>>>(jobs, n_jobs, tokens, cap, n_out);
     return cudaGetLastError();
 }
 

@@ -29,19 +29,7 @@
 #include <string>
 #include <vector>
 
-#include "ltl.h"
-#include "ltl_types.h"
-
-namespace ltl {
-cudaError_t launch_pack(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
-                        int W, int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
-                        cudaStream_t s);
-cudaError_t launch_eval(int W, const uint32_t *prog, int n_instr, const uint64_t *atoms, const uint64_t *mask,
-                        uint64_t stride, uint64_t plane, uint64_t *stack, int nsteps, uint32_t n_traces,
-                        uint64_t *out, int out_words, cudaStream_t s);
-bool compile_formula_program(const char *text, int n_props, std::vector<uint32_t> &prog, int &depth);
-ltl_status set_error(ltl_status s, const char *msg);
-}  // namespace ltl
+#include "ltl_internal.h"
 
 namespace {
 
@@ -53,8 +41,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_ptr[kMaxDevices] = {};
-
-uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
 
 // Device address of the static scratch on the current device (set-up once per
 // device; the symbol's name in host code is only a host-side handle).
@@ -100,13 +86,13 @@ extern "C" ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_le
     if (Wt > 16) return set_error(LTL_ERR_INVALID, "ltl_eval_noalloc: traces up to 1024 positions are supported");
     if (words_per_trace < W) return set_error(LTL_ERR_INVALID, "ltl_eval_noalloc: words_per_trace too small");
     if (n_traces == 0) return LTL_OK;
-    const uint64_t plane = round_up(n_traces, 128), stride = (uint64_t)Wt * plane;
+    const uint64_t plane = ltl::round_up(n_traces, 128), stride = (uint64_t)Wt * plane;
     // scratch layout: control block | program | masks | atoms | operand stack
     const uint64_t o_ctrl = 0;
-    const uint64_t o_prog = round_up(sizeof(Ctrl), 256);
-    const uint64_t o_mask = round_up(o_prog + 4 * prog.size(), 256);
-    const uint64_t o_atoms = round_up(o_mask + 8 * stride, 256);
-    const uint64_t o_stack = round_up(o_atoms + 8 * stride * (uint64_t)n_props, 256);
+    const uint64_t o_prog = ltl::round_up(sizeof(Ctrl), 256);
+    const uint64_t o_mask = ltl::round_up(o_prog + 4 * prog.size(), 256);
+    const uint64_t o_atoms = ltl::round_up(o_mask + 8 * stride, 256);
+    const uint64_t o_stack = ltl::round_up(o_atoms + 8 * stride * (uint64_t)n_props, 256);
     const uint64_t need = o_stack + 8 * stride * (uint64_t)depth;
     if (need > kNoallocScratchBytes) {
         char msg[256];

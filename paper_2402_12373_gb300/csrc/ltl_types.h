@@ -44,7 +44,8 @@ struct Seg {
     uint32_t n_ta, n_tb;   // tiles along a and along b
     int32_t a_inner;       // RECT: 1 = a-tile index varies fastest
     uint32_t ta, tb;       // tile extent along a (unary: run length) and along b
-    int32_t pad;
+    int32_t prob;          // index of the problem (engine slot) the segment belongs to
+    int32_t level;         // size level the candidates have
 };
 
 // Device control block (one per learn call).
@@ -53,7 +54,6 @@ struct Ctrl {
     unsigned long long cands;          // candidates processed (cumulative)
     unsigned long long compares;       // full-matrix compares after fingerprint match
     unsigned long long collisions;     // compares that found a different matrix
-    unsigned long long next_tile[kMaxLevels * 8];   // per (size level, connective)
     unsigned int found_count;          // separators seen (first one is recorded)
     int stop;                          // 1: CTAs leave at the next tile boundary
     int cap_hit;
@@ -87,14 +87,23 @@ struct Problem {
     unsigned long long spin_limit;
 };
 
-// One launch: the segments of one connective at one size level.
+// One launch: the segments of one connective for every problem of one launch
+// shape, each problem at its own size level.
 struct LevelArgs {
     const Seg *segs;
+    const Problem *probs;              // problem descriptors, indexed by Seg::prob
+    unsigned long long *tile_counter;  // this launch's tile counter (zeroed before)
     int32_t n_segs;
-    int32_t level;
-    uint64_t total_tiles;
-    int32_t counter;       // tile counter slot: level * 8 + connective
     int32_t pad;
+    uint64_t total_tiles;
+};
+
+// One formula reconstruction: the provenance array of a problem, its entry
+// count, and the provenance word of the root (a cache entry or a separator).
+struct WalkJob {
+    const uint64_t *prov;
+    uint64_t n_entries;
+    uint64_t root;
 };
 
 }  // namespace ltl

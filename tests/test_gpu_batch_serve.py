@@ -1,0 +1,118 @@
+"""Batched and served learning (many problems resident in one workspace,
+advanced in rounds, launches shared between problems) give every problem the
+result it gets alone: the same status, minimal size, completed levels and
+per-level unique and candidate counts; the returned formula separates under
+the oracle's semantics.  Counts are integers, so the comparison is exact."""
+import random
+import time
+
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O
+from paper_2402_12373_gb300 import _lib as L
+from paper_2402_12373_gb300 import synth
+
+
+@pytest.fixture(scope="module")
+def ws():
+    assert torch.cuda.is_available()
+    return L.default_workspace(4 << 30)
+
+
+def _mixed_problems(n, seed):
+    """Uneven problems: 1..4 props, 2..600 traces, lengths 0..70 (narrow and
+    wide layouts, several launch shapes), random connective masks."""
+    rng = random.Random(seed)
+    out = []
+    for i in range(n):
+        n_props = rng.choice([1, 2, 3, 4])
+        nt = rng.choice([2, 7, 20, 64, 150, 600])
+        maxlen = rng.choice([5, 12, 30, 45, 70])
+        tr = [[rng.randrange(1 << n_props) for _ in range(rng.randrange(0, maxlen + 1))] for _ in range(nt)]
+        h = rng.randrange(1, nt)
+        ops = L.ALL if rng.random() < 0.7 else rng.randrange(1, 128)
+        K = rng.choice([3, 4, 5])
+        out.append((synth.TraceSet.from_list(tr[:h]), synth.TraceSet.from_list(tr[h:]), n_props, ops, K))
+    return out
+
+
+def _alone(ws, problems, stop):
+    res = []
+    with L.Context(workspace=ws, stop=stop) as ctx:
+        for P, N, n_props, ops, K in problems:
+            res.append(ctx.learn(P, N, n_props, ops=ops, max_size=K))
+    return res
+
+
+def _same(a, b, K):
+    assert a["status"] == b["status"], (a, b)
+    assert a["size"] == b["size"]
+    assert a["levels_done"] == b["levels_done"]
+    d = a["levels_done"]
+    assert a["unique"][1:d + 1] == b["unique"][1:d + 1]
+    assert a["candidates"][1:d + 1] == b["candidates"][1:d + 1]
+
+
+@pytest.mark.parametrize("stop", [L.STOP_LEVEL, L.STOP_FIRST, L.STOP_NONE])
+def test_batch_equals_alone(ws, stop):
+    problems = _mixed_problems(40, 17)
+    alone = _alone(ws, problems, stop)
+    batch = L.learn_batch(problems, stop=stop, workspace=ws)
+    for (P, N, n_props, ops, K), a, b in zip(problems, alone, batch):
+        _same(a, b, K)
+        if b["status"] == "found":
+            assert O.separates(b["formula"], P, N, n_props), b["formula"]
+
+
+def test_batch_matches_oracle_on_plain_and_large(ws):
+    probs = [(synth.plain_single(seed=s).P, synth.plain_single(seed=s).N, 2, L.ALL, 7) for s in range(4)]
+    s = synth.single_large(n_each=256)
+    probs.append((s.P, s.N, 3, L.ALL, 6))
+    batch = L.learn_batch(probs, stop=L.STOP_LEVEL, workspace=ws)
+    for (P, N, n_props, ops, K), b in zip(probs, batch):
+        want = O.learn(P, N, n_props, ops=ops, max_size=K, stop_mode=2)
+        assert b["status"] == want["status"] and b["size"] == want["size"]
+        d = b["levels_done"]
+        assert d == want["levels_done"]
+        assert b["unique"][1:d + 1] == want["unique"][1:d + 1]
+
+
+def test_batch_admission_under_memory_pressure():
+    """A workspace too small for all problems at once: problems wait for
+    memory and still get their own results."""
+    problems = _mixed_problems(24, 23)
+    small = L.default_workspace(96 << 20)
+    alone = _alone(small, problems, L.STOP_LEVEL)
+    batch = L.learn_batch([p + (2 << 20,) for p in problems], stop=L.STOP_LEVEL, workspace=small)
+    for (P, N, n_props, ops, K), a, b in zip(problems, alone, batch):
+        if a["status"] == "cap" or b["status"] == "cap":
+            continue   # a 2 MiB budget can cap a problem that a bigger one completes
+        _same(a, b, K)
+
+
+def test_server_alone_vs_mix(ws):
+    """Requests that arrive while others run are admitted between rounds
+    (continuous batching); each result equals the problem's result alone."""
+    problems = _mixed_problems(30, 29)
+    alone = _alone(ws, problems, L.STOP_LEVEL)
+    with L.Server(workspace=ws, stop=L.STOP_LEVEL, max_resident=8) as srv:
+        ids = {}
+        results = {}
+        for i, (P, N, n_props, ops, K) in enumerate(problems):
+            ids[srv.submit(P, N, n_props, ops=ops, max_size=K)] = i
+            if i % 5 == 4:      # stagger arrivals
+                time.sleep(0.002)
+                for r in srv.poll(64, 0):
+                    results[ids[r["id"]]] = r
+        t0 = time.time()
+        while len(results) < len(problems) and time.time() - t0 < 120:
+            for r in srv.poll(64, 100):
+                results[ids[r["id"]]] = r
+        assert srv.pending() == (0, 0)
+    assert len(results) == len(problems)
+    for i, (P, N, n_props, ops, K) in enumerate(problems):
+        _same(alone[i], results[i], K)
+        assert results[i]["latency_ms"] >= results[i]["queue_ms"] >= 0.0
