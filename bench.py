@@ -38,6 +38,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -196,6 +198,160 @@ def cpu_baseline(target_s: float = 12.0, max_size: int = 6):
                       % (max_size, runs, secs)}
 
 
+def _units_all(r, T):
+    """candidates x traces over every level a run touched (the partial last
+    level included): the work both the batched and the one-at-a-time path do."""
+    return sum(r["candidates"][1:]) * T
+
+
+def _same_result(a, b):
+    d = a["levels_done"]
+    return (a["status"] == b["status"] and a["size"] == b["size"] and d == b["levels_done"]
+            and a["unique"][1:d + 1] == b["unique"][1:d + 1])
+
+
+def bench_batched(L, ws, problems):
+    """Batched workload: one ltl_learn_batch call against the plain path
+    (one ltl_ctx_learn per problem, same workspace, same memory budgets)."""
+    import torch
+    nbytes = ws.numel()
+    T = [p.n_traces for p in problems]
+    budgets = [int(0.85 * nbytes * t / sum(T)) for t in T]
+    items = [(p.P, p.N, p.n_props, L.ALL, p.planted_size + 2, b) for p, b in zip(problems, budgets)]
+    # plain path: one problem at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    alone = []
+    with L.Context(workspace=ws, stop=L.STOP_FIRST) as ctx:
+        for (P, N, n_props, ops, K, b) in items:
+            ctx.set_mem_budget(b)
+            alone.append(ctx.learn(P, N, n_props, ops=ops, max_size=K))
+    t_alone = time.perf_counter() - t0
+    # batched: every problem resident, one launch per connective and shape per round
+    t0 = time.perf_counter()
+    batch = L.learn_batch(items, stop=L.STOP_FIRST, workspace=ws)
+    t_batch = time.perf_counter() - t0
+    units = sum(_units_all(r, t) for r, t in zip(batch, T))
+    units_alone = sum(_units_all(r, t) for r, t in zip(alone, T))
+    same = all(_same_result(a, b) for a, b in zip(alone, batch))
+    st = {}
+    for r in batch:
+        st[r["status"]] = st.get(r["status"], 0) + 1
+    return {"workload": "batched: %d problems, props U{2..5}, |P|=|N| log-uniform 16..4096, length U{8..64}, "
+                        "Bernoulli(0.3), planted size U{3..9}, max size planted+2, stop at first separator, "
+                        "memory budget per problem proportional to |P|+|N|" % len(problems),
+            "problems": len(problems), "n_traces_total": sum(T),
+            "batched_s": t_batch, "one_at_a_time_s": t_alone,
+            "problems_per_s": len(problems) / t_batch, "one_at_a_time_problems_per_s": len(problems) / t_alone,
+            "speedup_vs_one_at_a_time": t_alone / t_batch,
+            "candidates_x_traces_per_s": units / t_batch,
+            "one_at_a_time_candidates_x_traces_per_s": units_alone / t_alone,
+            "results_equal_alone_and_batched": same, "statuses": st,
+            "rounds_max": max(r["rounds"] for r in batch)}
+
+
+def bench_served(L, ws, pool, rates=(0.5, 0.9, 1.5), per_rate_s=1.5, seed=5):
+    """Served workload: Poisson arrivals of trace-scaling-shaped problems
+    (65536 traces, length U{33..128}) at fractions of the one-at-a-time rate."""
+    import random as _random
+    import threading
+    import torch
+    # one-at-a-time rate mu on the same problems (host buffers, learn mode)
+    with L.Context(workspace=ws, stop=L.STOP_FIRST, mem_budget=2 << 30) as ctx:
+        for sp in pool[:2]:
+            ctx.learn(sp.P, sp.N, sp.n_props, max_size=11)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_alone = 0
+        alone = {}
+        while time.perf_counter() - t0 < 1.0 or n_alone < len(pool):
+            sp = pool[n_alone % len(pool)]
+            r = ctx.learn(sp.P, sp.N, sp.n_props, max_size=11)
+            alone[n_alone % len(pool)] = r
+            n_alone += 1
+        mu = n_alone / (time.perf_counter() - t0)
+    out = {"workload": "served: Poisson arrivals of trace-scaling problems (65536 traces, length U{33..128}, "
+                       "4 props, planted (((p0 U p1) & G !p3) & F p2), seeds 1000..%d cycled), max size 11, "
+                       "stop at first separator, 2 GiB per problem" % (1000 + len(pool) - 1),
+           "one_at_a_time_problems_per_s": mu, "rates": []}
+    rng = _random.Random(seed)
+    for f in rates:
+        lam = f * mu
+        n_req = max(8, int(lam * per_rate_s))
+        gaps = [rng.expovariate(lam) for _ in range(n_req)]
+        arrivals = []
+        acc = 0.0
+        for g in gaps:
+            acc += g
+            arrivals.append(acc)
+        results = {}
+        with L.Server(workspace=ws, stop=L.STOP_FIRST, max_resident=64, mem_budget=2 << 30) as srv:
+            ids = {}
+            t_start = time.perf_counter()
+
+            def submitter():
+                for i, t_a in enumerate(arrivals):
+                    dt = t_start + t_a - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    sp = pool[i % len(pool)]
+                    ids[srv.submit(sp.P, sp.N, sp.n_props, max_size=11)] = i
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            while len(results) < n_req and time.perf_counter() - t_start < 120:
+                for r in srv.poll(256, 50):
+                    results[r["id"]] = r
+            th.join()
+            t_end = time.perf_counter()
+        lat = sorted(r["latency_ms"] for r in results.values())
+        same = all(_same_result(alone[ids[i] % len(pool)], r) for i, r in results.items() if i in ids)
+        out["rates"].append({
+            "rate_fraction_of_mu": f, "arrival_rate_per_s": lam, "requests": n_req, "completed": len(results),
+            "throughput_problems_per_s": len(results) / (t_end - t_start),
+            "latency_ms_p50": lat[len(lat) // 2] if lat else None,
+            "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+            "results_equal_alone": same})
+    return out
+
+
+def bench_trace_scaling(L, ws, spec, steps=2):
+    """Trace-scaling workload: enumeration-only until the cache budget (120 GB)
+    or size 11 is reached; two-word sequences with cross-word carries."""
+    import torch
+    T = spec.n_traces
+    letters = np.concatenate([spec.P.letters, spec.N.letters]).astype(np.int32)
+    offs = np.concatenate([spec.P.offsets, spec.N.offsets[1:] + spec.P.offsets[-1]]).astype(np.int64)
+    dl = torch.from_numpy(letters).to(ws.device)
+    do = torch.from_numpy(offs).to(ws.device)
+    budget = min(120 * 10**9, int(0.9 * ws.numel()))
+    runs = []
+    with L.Context(workspace=ws, stop=L.STOP_NONE, mem_budget=budget) as ctx:
+        ctx.learn_device(dl, do, spec.P.n, spec.N.n, spec.max_len(), spec.n_props, max_size=11)   # warm-up
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = ctx.learn_device(dl, do, spec.P.n, spec.N.n, spec.max_len(), spec.n_props, max_size=11)
+            e1.record()
+            e1.synchronize()
+            runs.append((e0.elapsed_time(e1), r))
+    ms = statistics.mean(t for t, _ in runs)
+    r = runs[-1][1]
+    done = r["levels_done"]
+    units_done = sum(r["candidates"][1:done + 1]) * T
+    units_all = sum(r["candidates"][1:]) * T
+    return {"workload": "trace_scaling: 4 props, 32768+32768 traces, length U{33..128} (2 words per trace), "
+                        "Bernoulli(0.25), every level until size 11 or a 120 GB cache budget",
+            "status": r["status"], "levels_done": done, "unique": r["unique"][1:], "candidates": r["candidates"][1:],
+            "ms": ms, "level_ms": [round(x, 3) for x in r["ms"][1:]],
+            "candidates_x_traces_per_s_completed_levels": units_done / (ms / 1e3),
+            "candidates_x_traces_per_s_all": units_all / (ms / 1e3),
+            "launch": {"threads_per_cta": r["threads_per_cta"], "chunk_groups": r["chunk_groups"],
+                       "words_per_trace": r["words_per_trace"]},
+            "entries": r["entries"], "max_entries": r["max_entries"]}
+
+
 def run_reference(args):
     from paper_2402_12373_gb300 import dist
     rank, _, world = dist.env_rank()
@@ -235,6 +391,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-size", type=int, default=MAX_SIZE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched, served and trace-scaling measurements")
     ap.add_argument("--max-chunks", type=int, default=0,
                     help="launch-shape cap (16-byte chunks per thread); 0 = automatic")
     ap.add_argument("--ws-gb", type=float, default=0.0,
@@ -251,6 +409,15 @@ def main():
     from paper_2402_12373_gb300 import dist, synth
 
     rank, local_rank, world = dist.env_rank()
+    # inputs of the extra workloads, generated before any GPU work (spawn pool)
+    extra = None
+    if not args.no_extra and rank == 0:
+        procs = min(16, os.cpu_count() or 1)
+        batched_probs = synth.batched_workload(256, processes=procs)
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(8, procs)) as pool:
+            served_pool = pool.map(synth.trace_scaling, [1000 + i for i in range(8)])
+        extra = (batched_probs, served_pool)
     torch.cuda.set_device(local_rank)
     world = dist.init("nccl")
     dev = torch.device("cuda", local_rank)
@@ -382,6 +549,10 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        if extra is not None:
+            out["batched"] = bench_batched(L, ws, extra[0])
+            out["served"] = bench_served(L, ws, extra[1])
+            out["trace_scaling"] = bench_trace_scaling(L, ws, extra[1][0])
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))

@@ -167,6 +167,10 @@ typedef struct ltl_ctx ltl_ctx;
 ltl_status ltl_ctx_create(const ltl_opts *opts, ltl_ctx **out);
 void ltl_ctx_destroy(ltl_ctx *ctx);
 
+/* Device bytes for the cache and hash set of the context's next learn calls
+ * (as ltl_opts.mem_budget_bytes; 0 = all of the workspace). */
+ltl_status ltl_ctx_set_mem_budget(ltl_ctx *ctx, uint64_t bytes);
+
 /* As ltl_learn, on a context (host traces). */
 ltl_status ltl_ctx_learn(ltl_ctx *ctx, const ltl_traces *P, const ltl_traces *N, int n_props,
                          uint32_t ops, int max_size, char *formula_out, size_t formula_cap,

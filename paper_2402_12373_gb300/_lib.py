@@ -27,7 +27,7 @@ MAX_LEVELS = 64
 # Every symbol include/ltl.h declares.
 EXPORTS = ["ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_destroy", "ltl_ctx_learn",
            "ltl_ctx_learn_device", "ltl_ctx_level_range", "ltl_ctx_entry", "ltl_last_error",
-           "ltl_version", "ltl_eval_noalloc", "ltl_learn_batch", "ltl_server_create",
+           "ltl_version", "ltl_eval_noalloc", "ltl_learn_batch", "ltl_server_create", "ltl_ctx_set_mem_budget",
            "ltl_server_submit", "ltl_server_poll", "ltl_server_pending", "ltl_server_destroy"]
 FORMULA_MAX = 512
 
@@ -141,6 +141,8 @@ def load(build_if_missing: bool = True):
     L.ltl_ctx_entry.argtypes = [vp, u64, ctypes.c_char_p, ctypes.c_size_t, vp, i32]
     L.ltl_eval_noalloc.argtypes = [ctypes.c_char_p, vp, vp, u64, u32, i32, vp, i32, vp]
     L.ltl_eval_noalloc.restype = ctypes.c_int
+    L.ltl_ctx_set_mem_budget.argtypes = [vp, u64]
+    L.ltl_ctx_set_mem_budget.restype = ctypes.c_int
     L.ltl_learn_batch.argtypes = [i32, ctypes.POINTER(ProblemDesc), ctypes.POINTER(Opts), ctypes.POINTER(Result)]
     L.ltl_learn_batch.restype = ctypes.c_int
     L.ltl_server_create.argtypes = [ctypes.POINTER(Opts), i32, ctypes.POINTER(vp)]
@@ -249,6 +251,9 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_mem_budget(self, nbytes: int) -> None:
+        _check(self._L.ltl_ctx_set_mem_budget(self._h, int(nbytes)), ok=(LTL_OK,))
 
     def learn(self, P, N, n_props: int, ops: int = ALL, max_size: int = 7) -> Dict:
         hp, hn = _HostTraces(P), _HostTraces(N)

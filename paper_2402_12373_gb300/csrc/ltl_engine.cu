@@ -325,7 +325,20 @@ public:
         int blocks;
     };
     std::vector<Occ> occ;
-    cudaEvent_t ev_begin = nullptr, ev_end = nullptr, ev_op[kMaxGroups] = {};
+    std::vector<const void *> opted_in;
+
+    int max_dynamic_smem(const void *fn) const {
+        int optin = 0;
+        cudaFuncAttributes fa;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        return optin - (int)fa.sharedSizeBytes;
+    }
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+    std::vector<cudaEvent_t> ev_op;   // after each launch of a round, created on demand
     uint64_t total_rounds = 0;
 
     ~Engine() { teardown(); }
@@ -369,7 +382,6 @@ public:
         LTL_CUDA_TRY(cudaMallocHost(&h_ntok, sizeof(int) * max_slots));
         LTL_CUDA_TRY(cudaEventCreate(&ev_begin));
         LTL_CUDA_TRY(cudaEventCreate(&ev_end));
-        for (int i = 0; i < kMaxGroups; ++i) LTL_CUDA_TRY(cudaEventCreate(&ev_op[i]));
         slots.resize(max_slots);
         if (opts.workspace) {
             if (((uintptr_t)opts.workspace & 255u) != 0) return fail(LTL_ERR_INVALID, "workspace must be 256-byte aligned");
@@ -398,11 +410,9 @@ public:
         if (ev_begin) cudaEventDestroy(ev_begin);
         if (ev_end) cudaEventDestroy(ev_end);
         ev_begin = ev_end = nullptr;
-        for (int i = 0; i < kMaxGroups; ++i)
-            if (ev_op[i]) {
-                cudaEventDestroy(ev_op[i]);
-                ev_op[i] = nullptr;
-            }
+        for (auto &ev : ev_op)
+            if (ev) cudaEventDestroy(ev);
+        ev_op.clear();
         if (own_stream && stream) cudaStreamDestroy(stream);
         stream = nullptr;
         (void)cudaGetLastError();
@@ -465,7 +475,19 @@ public:
                 blocks = e.blocks;
                 return LTL_OK;
             }
-        if (smem > 0) LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // the opt-in limit is an attribute of the function (the last setter
+        // wins), so every level kernel is opted in once to the device maximum
+        if (std::find(opted_in.begin(), opted_in.end(), fn) == opted_in.end()) {
+            int optin = 0;
+            LTL_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+            cudaFuncAttributes fa;
+            LTL_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+            const int dyn = optin - (int)fa.sharedSizeBytes;
+            LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+            opted_in.push_back(fn);
+        }
+        if ((long long)smem > (long long)max_dynamic_smem(fn))
+            return fail(LTL_ERR_INVALID, "problem needs %zu bytes of shared memory per CTA", smem);
         int b = 0;
         LTL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, nt, smem));
         if (b < 1) return fail(LTL_ERR_INVALID, "level kernel cannot be resident (threads %d, smem %zu)", nt, smem);
@@ -652,6 +674,11 @@ public:
             }
             tiles[g] = total;
             grid[g] = (int)std::min<uint64_t>(total, cap);
+        }
+        while (ev_op.size() < groups.size()) {
+            cudaEvent_t ev = nullptr;
+            LTL_CUDA_TRY(cudaEventCreate(&ev));
+            ev_op.push_back(ev);
         }
         Seg *d_segs = (Seg *)(ws + o_segs);
         unsigned long long *d_counters = (unsigned long long *)(ws + o_counters);
@@ -942,6 +969,12 @@ ltl_status ltl_ctx_create(const ltl_opts *opts, ltl_ctx **out) {
 }
 
 void ltl_ctx_destroy(ltl_ctx *c) { delete c; }
+
+ltl_status ltl_ctx_set_mem_budget(ltl_ctx *c, uint64_t bytes) {
+    if (!c) return fail(LTL_ERR_INVALID, "ctx is NULL");
+    c->e.opts.mem_budget_bytes = bytes;
+    return LTL_OK;
+}
 
 ltl_status ltl_ctx_learn(ltl_ctx *c, const ltl_traces *P, const ltl_traces *N, int n_props, uint32_t ops,
                          int max_size, char *formula_out, size_t formula_cap, ltl_stats *stats) {

@@ -235,6 +235,9 @@ __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, 
     for (unsigned long long n = 0; n <= pb.hmask; ++n) {
         unsigned long long k = ld_volatile_u64(pb.hkeys + h);
         if (k == 0ull) {
+            // a full cache stores nothing more: an absent matrix is reported
+            // without claiming a slot, so the table keeps its load factor
+            if (ld_volatile_i32(&pb.ctrl->cap_hit)) return DEC_FAIL;
             k = atomicCAS(pb.hkeys + h, 0ull, key);
             if (k == 0ull) {
                 const unsigned long long i = atomicAdd(&pb.ctrl->n_entries, 1ull);

@@ -378,8 +378,13 @@ def random_tree(seed: int, counter: int, size: int, n_props: int):
     return _unrank(((hi << 64) | lo) % total, size, n_props, c)
 
 
-def batched_problem(i: int, base_seed: int = 0, max_len_each: int = 4096) -> Spec:
-    """Problem i of the batched workload (seed base_seed + i)."""
+def batched_problem(i: int, base_seed: int = 0, max_len_each: int = 4096, min_class_rate: float = 0.01) -> Spec:
+    """Problem i of the batched workload (seed base_seed + i): props U{2..5},
+    |P| = |N| = round(2^(4 + 8u)) (log-uniform 16..4096), length U{8..64},
+    Bernoulli(0.3) bits, a planted formula drawn uniformly among all syntax
+    trees of size U{3..9}.  A formula is redrawn when, on a probe of 4096
+    attempts, either class is accepted at a rate below `min_class_rate` (the
+    rejection fill would otherwise need millions of attempts)."""
     seed = base_seed + i
     s = np.uint64(seed)
     u = [splitmix64(s, _AUX_COUNTER + np.uint64(k)) for k in range(4)]
@@ -387,23 +392,25 @@ def batched_problem(i: int, base_seed: int = 0, max_len_each: int = 4096) -> Spe
     n_each = int(round(2 ** (4 + 8 * float(_uniform01(u[1])))))
     n_each = max(16, min(n_each, max_len_each))
     size = int(_uniform_int(u[2], 3, 9))
-    tries = 0
-    while True:
+    for tries in range(1000):
         f = random_tree(int(u[3]) + tries, 0, size, n_props)
         bits, lens = _attempts(seed * 1000003 + tries, 0, 4096, n_props, 8, 64, 0.3)
-        lab = label_at_zero(f, bits, lens, n_props)
-        frac = lab.mean()
-        tries += 1
-        # redraw formulae that (nearly) never or (nearly) always hold
-        if 0.0 < frac < 1.0 and min(lab.sum(), (~lab).sum()) * 1e5 >= 4096 * 1:
-            try:
-                P, N, _ = rejection_fill(seed * 1000003 + tries, f, n_each, n_each, n_props,
-                                         8, 64, 0.3, batch=8192, max_attempts=1 << 24)
-                return Spec(P, N, n_props, ast_str(f), size, "batched_%d" % i)
-            except RuntimeError:
-                pass
-        if tries > 1000:
-            raise RuntimeError("could not plant a formula for problem %d" % i)
+        frac = float(label_at_zero(f, bits, lens, n_props).mean())
+        if min_class_rate <= frac <= 1.0 - min_class_rate:
+            P, N, _ = rejection_fill(seed * 1000003 + 7919 * (tries + 1), f, n_each, n_each, n_props,
+                                     8, 64, 0.3, batch=8192, max_attempts=1 << 24)
+            return Spec(P, N, n_props, ast_str(f), size, "batched_%d" % i)
+    raise RuntimeError("could not plant a formula for problem %d" % i)
+
+
+def batched_workload(n: int = 256, base_seed: int = 0, processes: int = 0) -> List[Spec]:
+    """The n problems of the batched workload, generated in a spawn-started
+    process pool when processes > 1."""
+    if processes and processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.starmap(batched_problem, [(i, base_seed) for i in range(n)])
+    return [batched_problem(i, base_seed) for i in range(n)]
 
 
 def random_small(seed: int, n_traces: int, n_props: int, lo: int, hi: int,

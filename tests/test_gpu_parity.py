@@ -266,3 +266,15 @@ def _oracle_cached(P, N, n_props, K):
     if key not in _ORACLE_CACHE:
         _ORACLE_CACHE[key] = O.learn(P, N, n_props, max_size=K, stop_mode=0)
     return _ORACLE_CACHE[key]
+
+
+def test_context_reuse_across_shapes(ws):
+    """One context, problems of different launch shapes in turn (the same
+    kernel with more, then less, then more shared memory per CTA)."""
+    big = _long_traces(8, 2048, 33, 64)      # wide, 256 threads, 96 KiB of operand slots
+    small = _long_traces(9, 1024, 33, 64)    # wide, 128 threads, 48 KiB
+    with L.Context(workspace=ws, stop=L.STOP_NONE) as ctx:
+        for P, N in (big, small, big, small):
+            got = ctx.learn(P, N, 2, max_size=3)
+            want = _oracle_cached(P, N, 2, 3)
+            assert got["unique"][1:4] == want["unique"][1:4]
