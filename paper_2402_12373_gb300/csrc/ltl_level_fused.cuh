@@ -332,10 +332,11 @@ __device__ __forceinline__ void set_lane_problem(const Problem &pb, LaneConst &l
         }
 }
 
-// Register cap: 168 for 8 words per thread (three 128-thread CTAs per SM),
-// 128 for smaller shapes (at most 256 threads per CTA either way).
+// Register cap: 168 for 8 words per thread and for the narrow layout's
+// batches of four (three 128-thread CTAs per SM), 128 for the other shapes
+// (at most 256 threads per CTA either way).
 template <int W, int C, int NB, int OP, bool NARROW>
-__global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(LevelArgs la) {
+__global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kernel(LevelArgs la) {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     uint64_t *slots = reinterpret_cast<uint64_t *>(dyn_smem);
     __shared__ FusedShared<NB> sh;
@@ -356,6 +357,8 @@ __global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(LevelAr
     }
     __syncthreads();
     uint32_t phase = 0, round = 0;
+    int cur_prob = -1;
+    Problem pb;
     for (;;) {
         // thread 0 takes a tile and reads its problem's stop flag
         if (lc.tid == 0) {
@@ -375,12 +378,15 @@ __global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(LevelAr
         if (tile >= la.total_tiles) break;
         if (skip) continue;
         const Seg sg = la.segs[find_segment(la, tile)];
-        const Problem pb = la.probs[sg.prob];
+        if (sg.prob != cur_prob) {   // tiles of one problem usually come in runs
+            cur_prob = sg.prob;
+            pb = la.probs[sg.prob];
+            set_lane_problem<C, NARROW>(pb, lc);
+        }
         if ((uint64_t)dsmem < (uint64_t)(NB + 1) * pb.stride * 8ull) {   // slots must fit the launch's smem
             if (lc.tid == 0) atomicCAS(&pb.ctrl->err, 0, -1 /* LTL_ERR_INVALID */);
             continue;
         }
-        set_lane_problem<C, NARROW>(pb, lc);
         uint64_t a0, a1, b0, b1;
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
         unsigned long long done = 0;
@@ -391,11 +397,11 @@ __global__ void __maxnreg__((W * C >= 8) ? 168 : 128) fused_level_kernel(LevelAr
 
 }  // namespace lvl
 
-// candidates per batch: 2 when a thread holds 8 words per candidate or uses
-// the narrow layout (two traces per word), else 4
+// candidates per batch: 2 when a thread holds 8 words per candidate of the
+// wide layout, else 4
 template <int W, int C, bool NARROW>
 struct FusedNB {
-    static constexpr int value = (NARROW || W * C >= 8) ? 2 : 4;
+    static constexpr int value = (!NARROW && W * C >= 8) ? 2 : 4;
 };
 
 template <int W, int C, bool NARROW = false>
