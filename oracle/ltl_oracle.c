@@ -43,6 +43,17 @@
  *  - stop modes: 1 = stop at the first separator; 2 = finish the level where the
  *    first separator was found; 0 = enumerate every level up to max_size.
  *  - ops mask bits: Not=1 And=2 Or=4 X=8 F=16 G=32 U=64.
+ *
+ * Variants the paper states (oracle_learn_ex):
+ *  - cost homomorphism (Section 2): every connective and the atoms have a
+ *    positive cost; a formula's cost is the sum over its syntax tree.  Levels
+ *    are costs instead of sizes: atoms form level cost(atom); a unary
+ *    connective of cost k builds level c from level c - k; a binary one from
+ *    splits (i, j) with i + j = c - k.  Uniform cost (all 1) is the size.
+ *  - negation normal form (Section 2; used for the comparisons of Section 7):
+ *    negation is applied to atoms only.
+ *  - noisy learning (Section 3, after relaxedCheckAndCache): a candidate
+ *    separates when it misclassifies at most max_errors traces.
  */
 #define _POSIX_C_SOURCE 200809L
 #include <stdint.h>
@@ -139,13 +150,15 @@ static void sem_U(const Traces *S, const uint8_t *a, const uint8_t *b, uint8_t *
 }
 
 /* eq. (dagger): every positive true at position 0, every negative false there.
- * An empty trace is false at position 0 (i >= |tr|). */
-static int separates(const Traces *S, uint64_t n_pos, const uint8_t *m) {
+ * An empty trace is false at position 0 (i >= |tr|).  With an error budget
+ * (noisy learning) at most max_errors traces may be misclassified. */
+static int separates(const Traces *S, uint64_t n_pos, const uint8_t *m, uint64_t max_errors) {
+    uint64_t errors = 0;
     for (uint64_t t = 0; t < S->n; t++) {
         uint8_t v = tr_len(S, t) > 0 ? m[S->offsets[t]] : 0;
-        if (t < n_pos ? !v : v) return 0;
+        if (t < n_pos ? !v : v) errors++;
     }
-    return 1;
+    return errors <= max_errors;
 }
 
 /* ------------------------------------------------------------------ */
@@ -390,6 +403,9 @@ static void print_prov(const Cache *C, Prov pv, Str *s) {
 typedef struct {
     const Traces *S;
     uint64_t n_pos;
+    uint64_t max_errors;
+    int cost[8];          /* per connective (index = O_*), atoms at O_ATOM */
+    int nnf;              /* negation on atoms only */
     Cache C;
     uint64_t *lvl_begin, *lvl_end;   /* entries of level c: [begin, end) */
     uint64_t *unique, *cands;
@@ -405,7 +421,7 @@ typedef struct {
 /* check-and-cache for one candidate matrix m (owned).  Returns 1 to stop. */
 static int check_and_cache(Enum *E, int c, uint8_t *m, Prov pv) {
     E->cands[c]++;
-    if (separates(E->S, E->n_pos, m)) {
+    if (separates(E->S, E->n_pos, m, E->max_errors)) {
         if (!E->found) { E->found = 1; E->found_size = c; E->found_prov = pv; }
         if (E->stop_mode == 1) { free(m); return 1; }
     }
@@ -418,7 +434,7 @@ static int check_and_cache(Enum *E, int c, uint8_t *m, Prov pv) {
             k = (k + 1) & (E->C.nslot - 1);
         }
         free(m);
-        if (!dup) { E->cap_hit = 1; return 1; }
+        if (!dup) E->cap_hit = 1;   /* the level goes on: candidates are still checked */
         return 0;
     }
     int rc = cache_insert(&E->C, m, pv);
@@ -434,12 +450,15 @@ static uint8_t *new_mat(Enum *E) {
     return m;
 }
 
-/* Builds level c with connective op; returns 1 to stop. */
+/* Builds level c with connective op; returns 1 to stop.  The operands come
+ * from level c - cost(op) (unary) or from splits of c - cost(op) (binary). */
 static int handle_op(Enum *E, int op, int c) {
     const Traces *S = E->S;
+    const int rest = c - E->cost[op];
     if (op == O_F || op == O_G || op == O_X || op == O_NOT) {
-        if (c - 1 < 1) return 0;
-        for (uint64_t e = E->lvl_begin[c - 1]; e < E->lvl_end[c - 1]; e++) {
+        if (rest < 1) return 0;
+        if (op == O_NOT && E->nnf && rest != E->cost[O_ATOM]) return 0;   /* only atoms are negated */
+        for (uint64_t e = E->lvl_begin[rest]; e < E->lvl_end[rest]; e++) {
             uint8_t *m = new_mat(E);
             if (!m) return 1;
             const uint8_t *a = E->C.mat[e];
@@ -452,9 +471,9 @@ static int handle_op(Enum *E, int op, int c) {
         }
         return 0;
     }
-    /* binary: splits (cl, cr) with cl + cr = c - 1 */
-    for (int cl = 1; cl <= c - 2; cl++) {
-        int cr = c - 1 - cl;
+    /* binary: splits (cl, cr) with cl + cr = rest */
+    for (int cl = 1; cl <= rest - 1; cl++) {
+        int cr = rest - cl;
         if (op != O_U && cl > cr) continue;
         for (uint64_t a = E->lvl_begin[cl]; a < E->lvl_end[cl]; a++) {
             uint64_t b0 = E->lvl_begin[cr];
@@ -480,21 +499,26 @@ static double now_s(void) {
 }
 
 /*
- * oracle_learn: minimal separating formula by exhaustive enumeration.
+ * oracle_learn_ex: minimal-cost separating formula by exhaustive enumeration.
  *   letters/offsets : n_pos + n_neg traces, positives first
+ *   n_props         : alphabet size
  *   ops             : connective mask (Not=1 And=2 Or=4 X=8 F=16 G=32 U=64)
- *   max_size        : largest formula size tried (inclusive, <= 63)
+ *   max_size        : largest formula cost tried (inclusive, <= 63)
  *   stop_mode       : 1 first separator, 2 finish its level, 0 every level
  *   max_entries     : cache capacity in entries (0 = unlimited)
+ *   costs           : 8 costs indexed atom, Not, And, Or, X, F, G, U (NULL: all 1)
+ *   nnf             : nonzero = negation on atoms only
+ *   max_errors      : misclassified traces a separator may have (0 = exact)
  *   formula_out     : text of the first separator found ("" if none)
- *   unique, cands, secs : per size level 0..max_size (caller-allocated, max_size+1)
+ *   unique, cands, secs : per cost level 0..max_size (caller-allocated, max_size+1)
  *   levels_done     : number of levels fully enumerated
  * Returns OR_FOUND, OR_NOT_FOUND, OR_CAP, or an error.
  */
-int oracle_learn(const uint32_t *letters, const uint64_t *offsets, uint64_t n_pos, uint64_t n_neg,
-                 int n_props, uint32_t ops, int max_size, int stop_mode, uint64_t max_entries,
-                 char *formula_out, size_t formula_cap, int *found_size,
-                 uint64_t *unique, uint64_t *cands, double *secs, int *levels_done) {
+int oracle_learn_ex(const uint32_t *letters, const uint64_t *offsets, uint64_t n_pos, uint64_t n_neg,
+                    int n_props, uint32_t ops, int max_size, int stop_mode, uint64_t max_entries,
+                    const int *costs, int nnf, uint64_t max_errors,
+                    char *formula_out, size_t formula_cap, int *found_size,
+                    uint64_t *unique, uint64_t *cands, double *secs, int *levels_done) {
     if (n_props < 1 || n_props > 32 || max_size < 1 || max_size > 63 || !found_size || !levels_done)
         return OR_INVALID;
     Traces S = {letters, offsets, n_pos + n_neg, offsets[n_pos + n_neg]};
@@ -502,7 +526,11 @@ int oracle_learn(const uint32_t *letters, const uint64_t *offsets, uint64_t n_po
         if (n_props < 32 && (letters[q] >> n_props)) return OR_INVALID;
     Enum E;
     memset(&E, 0, sizeof E);
-    E.S = &S; E.n_pos = n_pos; E.stop_mode = stop_mode;
+    E.S = &S; E.n_pos = n_pos; E.stop_mode = stop_mode; E.max_errors = max_errors; E.nnf = nnf;
+    for (int k = 0; k < 8; k++) {
+        E.cost[k] = costs ? costs[k] : 1;
+        if (E.cost[k] < 1) return OR_INVALID;
+    }
     E.max_entries = max_entries ? max_entries : (uint64_t)-1;
     E.C.W = S.total;
     E.lvl_begin = (uint64_t *)calloc((size_t)max_size + 2, sizeof(uint64_t));
@@ -519,13 +547,13 @@ int oracle_learn(const uint32_t *letters, const uint64_t *offsets, uint64_t n_po
     for (int c = 1; c <= max_size && !stop && !E.err; c++) {
         double t0 = now_s();
         E.lvl_begin[c] = E.C.n;
-        if (c == 1) {
+        if (c == E.cost[O_ATOM]) {
             for (int p = 0; p < n_props && !stop; p++) {
                 uint8_t *m = new_mat(&E);
                 if (!m) { stop = 1; break; }
                 sem_atom(&S, p, m);
                 Prov pv = {O_ATOM, (uint32_t)p, 0};
-                stop = check_and_cache(&E, 1, m, pv);
+                stop = check_and_cache(&E, c, m, pv);
             }
         } else {
             for (int k = 0; k < 7 && !stop; k++)
@@ -533,7 +561,8 @@ int oracle_learn(const uint32_t *letters, const uint64_t *offsets, uint64_t n_po
         }
         E.lvl_end[c] = E.C.n;
         secs[c] = now_s() - t0;
-        if (!stop && !E.err) *levels_done = c;
+        if (!stop && !E.err && !E.cap_hit) *levels_done = c;
+        if (E.cap_hit) stop = 1;
         if (E.found && stop_mode != 0) stop = 1;
     }
     int rc;
@@ -553,4 +582,13 @@ int oracle_learn(const uint32_t *letters, const uint64_t *offsets, uint64_t n_po
     cache_free(&E.C);
     free(E.lvl_begin); free(E.lvl_end);
     return rc;
+}
+
+/* oracle_learn: uniform cost, all connectives' negation, exact separation. */
+int oracle_learn(const uint32_t *letters, const uint64_t *offsets, uint64_t n_pos, uint64_t n_neg,
+                 int n_props, uint32_t ops, int max_size, int stop_mode, uint64_t max_entries,
+                 char *formula_out, size_t formula_cap, int *found_size,
+                 uint64_t *unique, uint64_t *cands, double *secs, int *levels_done) {
+    return oracle_learn_ex(letters, offsets, n_pos, n_neg, n_props, ops, max_size, stop_mode, max_entries,
+                           NULL, 0, 0, formula_out, formula_cap, found_size, unique, cands, secs, levels_done);
 }

@@ -59,6 +59,15 @@ def _load():
                                          ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int)]
             lib.oracle_learn.restype = ctypes.c_int
+            lib.oracle_learn_ex.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.c_char_p, ctypes.c_size_t,
+                                            ctypes.POINTER(ctypes.c_int), u64p, u64p,
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_learn_ex.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -110,11 +119,13 @@ def separates(formula: str, P, N, n_props: int) -> bool:
 
 
 def learn(P, N, n_props: int, ops: int = OPS_ALL, max_size: int = 7, stop_mode: int = 1,
-          max_entries: int = 0) -> Dict:
+          max_entries: int = 0, costs=None, nnf: bool = False, max_errors: int = 0) -> Dict:
     """Exhaustive enumeration (Section 3) with exact dedup.
 
     stop_mode: 1 = stop at the first separator, 2 = finish that level,
-    0 = enumerate every level up to max_size.
+    0 = enumerate every level up to max_size.  costs: 8 connective costs
+    (atom, Not, And, Or, X, F, G, U), levels are then costs; nnf: negation on
+    atoms only; max_errors: misclassified traces a separator may have.
     """
     letters, offsets = _concat(P, N)
     nP, nN = P.offsets.shape[0] - 1, N.offsets.shape[0] - 1
@@ -125,9 +136,13 @@ def learn(P, N, n_props: int, ops: int = OPS_ALL, max_size: int = 7, stop_mode: 
     fsz = ctypes.c_int(0)
     done = ctypes.c_int(0)
     buf = ctypes.create_string_buffer(1 << 16)
-    rc = _load().oracle_learn(letters.ctypes.data, offsets.ctypes.data, nP, nN, n_props, ops,
-                              K, stop_mode, max_entries, buf, len(buf), ctypes.byref(fsz),
-                              uniq, cand, secs, ctypes.byref(done))
+    carr = None
+    if costs is not None:
+        carr = (ctypes.c_int * 8)(*[int(x) for x in costs])
+    rc = _load().oracle_learn_ex(letters.ctypes.data, offsets.ctypes.data, nP, nN, n_props, ops,
+                                 K, stop_mode, max_entries, ctypes.cast(carr, ctypes.c_void_p) if carr else None,
+                                 1 if nnf else 0, int(max_errors), buf, len(buf), ctypes.byref(fsz),
+                                 uniq, cand, secs, ctypes.byref(done))
     if rc < 0:
         raise RuntimeError("oracle_learn failed: %s" % STATUS.get(rc, rc))
     return {

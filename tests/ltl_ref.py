@@ -178,12 +178,46 @@ def all_trees(n_props: int, ops: int, max_size: int) -> Dict[int, List]:
     return trees
 
 
+COST_INDEX = {"p": 0, "!": 1, "&": 2, "|": 3, "X": 4, "F": 5, "G": 6, "U": 7}
+
+
+def cost(f, costs) -> int:
+    """Cost of a syntax tree under a cost homomorphism (Section 2)."""
+    return costs[COST_INDEX[f[0]]] + sum(cost(c, costs) for c in f[1:] if isinstance(c, tuple))
+
+
+def trees_by_cost(n_props: int, ops: int, max_cost: int, costs, nnf: bool = False) -> Dict[int, List]:
+    """Every syntax tree of cost <= max_cost, by cost (NNF: ! over atoms only)."""
+    out: Dict[int, List] = {c: [] for c in range(1, max_cost + 1)}
+    if costs[0] <= max_cost:
+        out[costs[0]] = [("p", p) for p in range(n_props)]
+    un = [o for o in UNARY if ops & OPBIT[o]]
+    bi = [o for o in BINARY if ops & OPBIT[o]]
+    for c in range(1, max_cost + 1):
+        for o in un:
+            r = c - costs[COST_INDEX[o]]
+            if r >= 1:
+                src = out[r] if not (nnf and o == "!") else [t for t in out[r] if t[0] == "p"]
+                out[c] += [(o, t) for t in src]
+        for o in bi:
+            r = c - costs[COST_INDEX[o]]
+            for i in range(1, r):
+                out[c] += [(o, a, b) for a in out[i] for b in out[r - i]]
+    return out
+
+
+def errors(f, P, N) -> int:
+    return sum(1 for tr in P if not holds(f, tr, 0)) + sum(1 for tr in N if holds(f, tr, 0))
+
+
 def brute_force(P: List[List[int]], N: List[List[int]], n_props: int, ops: int,
-                max_size: int) -> Dict:
-    """Unique characteristic matrices per size and the minimal separating size,
-    from every syntax tree (no cache, no dedup, no compositional shortcut)."""
+                max_size: int, costs=None, nnf: bool = False, max_errors: int = 0) -> Dict:
+    """Unique characteristic matrices per cost level and the minimal cost of a
+    formula misclassifying at most max_errors traces, from every syntax tree
+    (no cache, no dedup, no compositional shortcut)."""
+    costs = list(costs) if costs is not None else [1] * 8
     traces = list(P) + list(N)
-    trees = all_trees(n_props, ops, max_size)
+    trees = trees_by_cost(n_props, ops, max_size, costs, nnf)
     seen = set()
     unique = [0] * (max_size + 1)
     min_size: Optional[int] = None
@@ -193,9 +227,8 @@ def brute_force(P: List[List[int]], N: List[List[int]], n_props: int, ops: int,
             cm = tuple(tuple(truth(t, tr)) for tr in traces)
             if cm not in seen:
                 new.add(cm)
-            if min_size is None:
-                if all(holds(t, tr, 0) for tr in P) and not any(holds(t, tr, 0) for tr in N):
-                    min_size = s
+            if min_size is None and errors(t, P, N) <= max_errors:
+                min_size = s
         unique[s] = len(new)
         seen |= new
     return {"unique": unique, "min_size": min_size}

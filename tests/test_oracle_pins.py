@@ -345,3 +345,47 @@ def test_unsolvable_and_cap():
     s = synth.plain_single()
     r = O.learn(s.P, s.N, 2, max_size=7, stop_mode=0, max_entries=50)
     assert r["status"] in ("cap", "found")
+
+
+# ------------------------------------------------ costs, NNF, noisy learning
+
+VARIANTS = [
+    dict(costs=[1, 1, 1, 1, 1, 1, 1, 1], nnf=False, max_errors=0),
+    dict(costs=[1, 2, 1, 1, 1, 1, 1, 1], nnf=False, max_errors=0),
+    dict(costs=[2, 1, 3, 1, 2, 1, 2, 3], nnf=False, max_errors=0),
+    dict(costs=[1, 1, 1, 1, 1, 1, 1, 1], nnf=True, max_errors=0),
+    dict(costs=[1, 1, 2, 2, 1, 1, 1, 9], nnf=True, max_errors=0),
+    dict(costs=[1, 1, 1, 1, 1, 1, 1, 1], nnf=False, max_errors=1),
+    dict(costs=[1, 1, 1, 1, 1, 1, 1, 1], nnf=False, max_errors=2),
+]
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=lambda v: "c%s_nnf%d_e%d" % ("".join(map(str, v["costs"])), v["nnf"], v["max_errors"]))
+@pytest.mark.parametrize("spec", _tiny_specs()[:4])
+def test_variants_equal_brute_force(spec, variant):
+    """Cost homomorphism (levels = costs), negation normal form and noisy
+    learning, against every syntax tree of cost <= K."""
+    P, N, n_props = spec
+    K = 6 if n_props == 1 else 5
+    bf = R.brute_force(P, N, n_props, 127, K, **variant)
+    r = O.learn(_ts(P), _ts(N), n_props, max_size=K, stop_mode=0, **variant)
+    assert r["unique"][1:] == bf["unique"][1:]
+    assert r["size"] == bf["min_size"]
+    if r["formula"] is not None:
+        f = R.parse(r["formula"])
+        assert R.cost(f, variant["costs"]) == r["size"]
+        assert R.errors(f, P, N) <= variant["max_errors"]
+        if variant["nnf"]:
+            def nnf_ok(t):
+                if t[0] == "!":
+                    return t[1][0] == "p"
+                return all(nnf_ok(c) for c in t[1:] if isinstance(c, tuple))
+            assert nnf_ok(f)
+
+
+def test_high_cost_bans_a_connective():
+    """Section 2: a connective of cost above the budget is never used."""
+    s = synth.plain_single()
+    r = O.learn(s.P, s.N, 2, max_size=7, costs=[1, 1, 1, 1, 1, 50, 1, 1])   # F banned
+    assert r["status"] == "found" and "F" not in r["formula"]
+    assert r["size"] >= 5
