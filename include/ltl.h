@@ -56,7 +56,10 @@ typedef enum {
 
 enum {
     LTL_NOT = 1, LTL_AND = 2, LTL_OR = 4, LTL_X = 8,
-    LTL_F = 16, LTL_G = 32, LTL_U = 64, LTL_ALL = 127
+    LTL_F = 16, LTL_G = 32, LTL_U = 64, LTL_ALL = 127,
+    /* restriction flag in the same mask: negation normal form, i.e. negation
+     * applied to atoms only (Section 2; used for the comparisons of Section 7) */
+    LTL_NNF = 256
 };
 
 /* stop_on_solution values */
@@ -64,6 +67,27 @@ enum {
     LTL_STOP_NONE = 0,     /* enumerate every level up to max_size           */
     LTL_STOP_FIRST = 1,    /* return at the first separating candidate       */
     LTL_STOP_LEVEL = 2     /* finish the level where a separator was found   */
+};
+
+/* ruc values: the cache admission policy (relaxed uniqueness checks, Section 5).
+ * A candidate enters the cache only if its admission key is new.
+ *   LTL_RUC_EXACT  key = the whole characteristic matrix (fingerprint, then a
+ *                  full compare): every distinct matrix is kept.
+ *   LTL_RUC_HASH   key = 63 bits of a hash of the matrix, no compare: a key
+ *                  collision drops a matrix (false positive, never a false
+ *                  negative).  A matrix of at most 63 bits in all (the sum of
+ *                  the trace lengths; traces x max_len for device-resident
+ *                  traces) is checked exactly instead.
+ *   LTL_RUC_FKP    key = the first b positions of every trace concatenated in
+ *                  trace order, b = max(1, 63 / n_traces), truncated to 63 bits
+ *                  (the "first k percent" map of Section 7).
+ * Relaxed modes stay sound (every returned formula separates) but may miss the
+ * minimal size, and results may vary between runs: which of two colliding
+ * matrices is kept depends on timing. */
+enum {
+    LTL_RUC_EXACT = 0,
+    LTL_RUC_HASH = 1,
+    LTL_RUC_FKP = 2
 };
 
 typedef struct {
@@ -93,6 +117,19 @@ typedef struct {
     uint32_t max_chunks;         /* launch-shape cap: at most this many 16-byte
                                     chunks per thread (rounded up to a power of
                                     two); 0 = automatic                        */
+    uint32_t costs[8];           /* cost homomorphism (Section 2): cost of the
+                                    atoms, !, &, |, X, F, G, U in this order;
+                                    0 = 1.  Size levels become cost levels and
+                                    max_size is then the largest cost; a cost
+                                    above max_size bans a connective          */
+    uint32_t max_errors;         /* noisy learning (Section 3): a formula that
+                                    misclassifies at most this many traces
+                                    counts as separating; 0 = exact           */
+    uint32_t ruc;                /* cache admission (Section 5): LTL_RUC_EXACT
+                                    (default), LTL_RUC_HASH or LTL_RUC_FKP    */
+    uint32_t ruc_mask_bits;      /* relaxed modes: zero this many of the 63
+                                    admission-key bits, the highest first
+                                    (0..62; the masking experiment, Sec. 7)   */
 } ltl_opts;
 
 #define LTL_MAX_LEVELS 64
@@ -131,7 +168,8 @@ typedef struct {
  *              disjoint; a trace in both makes the problem unsolvable and the
  *              result is LTL_NOT_FOUND.
  *   n_props    alphabet size, 1..32; every letter must be < 2^n_props.
- *   ops        connectives allowed (mask of LTL_NOT .. LTL_U).
+ *   ops        connectives allowed (mask of LTL_NOT .. LTL_U), optionally
+ *              with LTL_NNF.
  *   max_size   largest formula size (syntax-tree nodes) tried, 1..63.
  *   opts       may be NULL.
  *   formula_out, formula_cap  receive the NUL-terminated text of a separating

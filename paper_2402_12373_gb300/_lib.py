@@ -21,6 +21,8 @@ LTL_ERR_INVALID, LTL_ERR_CUDA, LTL_ERR_OOM, LTL_ERR_TIMEOUT, LTL_ERR_BUFSIZE = -
 STATUS = {0: "found", 1: "not_found", 2: "cap", -1: "invalid", -2: "cuda", -3: "oom", -4: "timeout",
           -5: "bufsize"}
 NOT, AND, OR, X, F, G, U, ALL = 1, 2, 4, 8, 16, 32, 64, 127
+NNF = 256   # negation on atoms only (flag in the ops mask)
+RUC_EXACT, RUC_HASH, RUC_FKP = 0, 1, 2   # cache admission policies
 STOP_NONE, STOP_FIRST, STOP_LEVEL = 0, 1, 2
 MAX_LEVELS = 64
 
@@ -51,7 +53,8 @@ class Opts(ctypes.Structure):
                 ("spin_limit", ctypes.c_uint64), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("user", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_uint64), ("autotune_path", ctypes.c_char_p),
-                ("max_chunks", ctypes.c_uint32)]
+                ("max_chunks", ctypes.c_uint32), ("costs", ctypes.c_uint32 * 8),
+                ("max_errors", ctypes.c_uint32), ("ruc", ctypes.c_uint32), ("ruc_mask_bits", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -186,7 +189,11 @@ class _HostTraces:
 
 
 def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int = 0,
-          spin_limit: int = 0, max_chunks: int = 0) -> Opts:
+          spin_limit: int = 0, max_chunks: int = 0, costs=None, max_errors: int = 0, ruc: int = RUC_EXACT,
+          ruc_mask_bits: int = 0) -> Opts:
+    """costs: 8 connective costs (atoms, !, &, |, X, F, G, U), None = all 1;
+    max_errors: misclassified traces a separator may have; ruc, ruc_mask_bits:
+    cache admission policy and masked admission-key bits."""
     o = Opts()
     o.mem_budget_bytes = int(mem_budget)
     o.stop_on_solution = int(stop)
@@ -199,6 +206,14 @@ def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int =
     o.workspace_bytes = 0
     o.autotune_path = None
     o.max_chunks = int(max_chunks)
+    if costs is not None:
+        if len(costs) != 8 or min(costs) < 1:
+            raise ValueError("costs: eight positive integers (atoms, !, &, |, X, F, G, U)")
+        for i, c in enumerate(costs):
+            o.costs[i] = int(c)
+    o.max_errors = int(max_errors)
+    o.ruc = int(ruc)
+    o.ruc_mask_bits = int(ruc_mask_bits)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -223,14 +238,16 @@ class Context:
     """A reusable learner context: stream + torch workspace + last cache."""
 
     def __init__(self, workspace=None, stop: int = STOP_FIRST, stream=None, mem_budget: int = 0,
-                 spin_limit: int = 0, workspace_bytes: Optional[int] = None, max_chunks: int = 0):
+                 spin_limit: int = 0, workspace_bytes: Optional[int] = None, max_chunks: int = 0,
+                 costs=None, max_errors: int = 0, ruc: int = RUC_EXACT, ruc_mask_bits: int = 0):
         self._L = load()
         if workspace is None:
             workspace = default_workspace(workspace_bytes)
         self.workspace = workspace
         if stream is None:
             stream = _current_stream()
-        self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit, max_chunks)
+        self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit, max_chunks, costs, max_errors, ruc,
+                           ruc_mask_bits)
         h = ctypes.c_void_p()
         _check(self._L.ltl_ctx_create(ctypes.byref(self._opts), ctypes.byref(h)), ok=(LTL_OK,))
         self._h = h
@@ -295,11 +312,13 @@ def _result(rc: int, buf, st: Stats, max_size: int) -> Dict:
 
 
 def learn(P, N, n_props: int, ops: int = ALL, max_size: int = 7, stop: int = STOP_FIRST,
-          workspace=None, mem_budget: int = 0) -> Dict:
+          workspace=None, mem_budget: int = 0, costs=None, max_errors: int = 0, ruc: int = RUC_EXACT,
+          ruc_mask_bits: int = 0) -> Dict:
     """One-shot ltl_learn with host traces (TraceSet-like P and N)."""
     L = load()
     hp, hn = _HostTraces(P), _HostTraces(N)
-    o = _opts(stop, workspace, _current_stream() if workspace is not None else None, mem_budget)
+    o = _opts(stop, workspace, _current_stream() if workspace is not None else None, mem_budget, 0, 0, costs,
+              max_errors, ruc, ruc_mask_bits)
     buf = ctypes.create_string_buffer(8 * max_size + 64)
     st = Stats()
     rc = L.ltl_learn(ctypes.byref(hp.struct), ctypes.byref(hn.struct), n_props, ops, max_size,
@@ -342,7 +361,8 @@ def _problem_desc(P, N, n_props: int, ops: int, max_size: int, budget: int = 0):
 
 
 def learn_batch(problems: Sequence, stop: int = STOP_FIRST, workspace=None, mem_budget: int = 0,
-                max_chunks: int = 0) -> List[Dict]:
+                max_chunks: int = 0, costs=None, max_errors: int = 0, ruc: int = RUC_EXACT,
+                ruc_mask_bits: int = 0) -> List[Dict]:
     """ltl_learn_batch.  problems: sequence of (P, N, n_props, ops, max_size[, budget])."""
     L = load()
     n = len(problems)
@@ -355,7 +375,8 @@ def learn_batch(problems: Sequence, stop: int = STOP_FIRST, workspace=None, mem_
         descs[i] = d
         keep.append(k)
     out = (Result * max(n, 1))()
-    o = _opts(stop, workspace, _current_stream() if workspace is not None else None, mem_budget, 0, max_chunks)
+    o = _opts(stop, workspace, _current_stream() if workspace is not None else None, mem_budget, 0, max_chunks,
+              costs, max_errors, ruc, ruc_mask_bits)
     _check(L.ltl_learn_batch(n, descs, ctypes.byref(o), out), ok=(LTL_OK,))
     return [out[i].to_dict() for i in range(n)]
 
@@ -364,12 +385,13 @@ class Server:
     """ltl_server_*: continuous batching of submitted learning problems."""
 
     def __init__(self, workspace=None, stop: int = STOP_FIRST, max_resident: int = 64, mem_budget: int = 0,
-                 workspace_bytes: Optional[int] = None, max_chunks: int = 0):
+                 workspace_bytes: Optional[int] = None, max_chunks: int = 0, costs=None,
+                 max_errors: int = 0, ruc: int = RUC_EXACT, ruc_mask_bits: int = 0):
         self._L = load()
         if workspace is None:
             workspace = default_workspace(workspace_bytes)
         self.workspace = workspace
-        self._opts = _opts(stop, workspace, None, mem_budget, 0, max_chunks)
+        self._opts = _opts(stop, workspace, None, mem_budget, 0, max_chunks, costs, max_errors, ruc, ruc_mask_bits)
         h = ctypes.c_void_p()
         _check(self._L.ltl_server_create(ctypes.byref(self._opts), max_resident, ctypes.byref(h)), ok=(LTL_OK,))
         self._h = h

@@ -247,35 +247,44 @@ uint64_t seg_candidates(const Seg &s) {
     return s.a_count * s.b_count;
 }
 
-// Candidate space of size level k of one problem (Section 3, handleOp), in
-// the paper's connective order F, U, G, X, And, Or, Not.
-void level_segments(const Slot &s, int k, int prob, std::vector<Seg> &out) {
+// Cost of each connective (index = op; atoms at OP_ATOM), 0 read as 1.
+struct Costs {
+    int c[8];
+};
+
+// Candidate space of cost level k of one problem (Section 3, handleOp, with the
+// cost homomorphism of Section 2; uniform cost = size), in the paper's
+// connective order F, U, G, X, And, Or, Not.
+void level_segments(const Slot &s, int k, int prob, const Costs &cost, std::vector<Seg> &out) {
     auto push = [&](Seg sg) {
         sg.prob = prob;
         sg.level = k;
         out.push_back(sg);
     };
-    if (k == 1) {
+    if (k == cost.c[OP_ATOM]) {
         Seg sg{};
         sg.op = OP_ATOM; sg.kind = SEG_UNARY; sg.a_begin = 0; sg.a_count = (uint64_t)s.in.n_props;
         push(sg);
-        return;
+        return;   // no other formula has the atoms' cost
     }
     const int order[7] = {OP_F, OP_U, OP_G, OP_X, OP_AND, OP_OR, OP_NOT};
     const uint32_t bit[8] = {0, LTL_NOT, LTL_AND, LTL_OR, LTL_X, LTL_F, LTL_G, LTL_U};
     for (int oi = 0; oi < 7; ++oi) {
         const int op = order[oi];
         if (!(s.in.ops & bit[op])) continue;
+        const int rest = k - cost.c[op];
         if (op == OP_F || op == OP_G || op == OP_X || op == OP_NOT) {
-            const uint64_t cnt = s.lvl_count[k - 1];
+            if (rest < 1) continue;
+            if (op == OP_NOT && (s.in.ops & LTL_NNF) && rest != cost.c[OP_ATOM]) continue;   // atoms only
+            const uint64_t cnt = s.lvl_count[rest];
             if (!cnt) continue;
             Seg sg{};
-            sg.op = op; sg.kind = SEG_UNARY; sg.a_begin = s.lvl_begin[k - 1]; sg.a_count = cnt;
+            sg.op = op; sg.kind = SEG_UNARY; sg.a_begin = s.lvl_begin[rest]; sg.a_count = cnt;
             push(sg);
             continue;
         }
-        for (int cl = 1; cl <= k - 2; ++cl) {
-            const int cr = k - 1 - cl;
+        for (int cl = 1; cl <= rest - 1; ++cl) {
+            const int cr = rest - cl;
             if (op != OP_U && cl > cr) continue;
             const uint64_t na = s.lvl_count[cl], nb = s.lvl_count[cr];
             if (!na || !nb) continue;
@@ -345,6 +354,8 @@ public:
 
     ltl_status setup(const ltl_opts *o, int max_resident, bool keep) {
         opts = *o;
+        if (opts.ruc > LTL_RUC_FKP) return fail(LTL_ERR_INVALID, "ruc must be LTL_RUC_EXACT, LTL_RUC_HASH or LTL_RUC_FKP");
+        if (opts.ruc_mask_bits > 62) return fail(LTL_ERR_INVALID, "ruc_mask_bits must be at most 62");
         keep_finished = keep;
         max_slots = std::max(1, std::min(max_resident, 4096));
         cudaError_t e = cudaGetDevice(&device);
@@ -573,6 +584,14 @@ public:
         pb.nsteps = L.nsteps;
         pb.stop_first = opts.stop_on_solution == LTL_STOP_FIRST ? 1 : 0;
         pb.groups = L.G;
+        pb.max_errors = opts.max_errors;
+        // admission policy: a matrix of at most 63 bits is its own key, so the
+        // hashed check of such a matrix is the exact one (Section 5)
+        pb.ruc = opts.ruc;
+        const uint64_t cm_bits = s.in.device_input ? T * s.in.max_len : s.in.total_pos;
+        if (pb.ruc == RUC_HASH && cm_bits <= 63) pb.ruc = RUC_EXACT;
+        pb.fkp_b = (uint32_t)std::max<uint64_t>(1, 63 / std::max<uint64_t>(T, 1));
+        pb.key_mask = kKey63 >> std::min<uint32_t>(opts.ruc_mask_bits, 62);
         pb.spin_limit = opts.spin_limit ? opts.spin_limit : (1ull << 20);
         LTL_CUDA_TRY(cudaMemcpyAsync((Problem *)(ws + o_probs) + si, &h_probs[si], sizeof(Problem),
                                      cudaMemcpyHostToDevice, stream));
@@ -605,6 +624,10 @@ public:
 
     // One round: the next size level of every running problem.
     ltl_status round() {
+        Costs cost;
+        // 0 reads as 1; anything above the largest level only bans the connective
+        for (int i = 0; i < 8; ++i)
+            cost.c[i] = opts.costs[i] ? (int)std::min<uint32_t>(opts.costs[i], kMaxLevels) : 1;
         std::vector<Seg> segs;
         std::vector<int> ran;   // slots that enumerate a level this round
         for (int si = 0; si < max_slots; ++si) {
@@ -613,7 +636,7 @@ public:
                 const int k = s.level;
                 s.lvl_begin[k] = s.prev_entries;
                 const size_t before = segs.size();
-                level_segments(s, k, si, segs);
+                level_segments(s, k, si, cost, segs);
                 if (segs.size() > before) {
                     ran.push_back(si);
                     break;

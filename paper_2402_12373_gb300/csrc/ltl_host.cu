@@ -183,7 +183,7 @@ ltl_status write_formula(const std::string &s, char *out, size_t cap) {
 ltl_status check_common(int n_props, uint32_t ops, int max_size) {
     if (n_props < 1 || n_props > 32) return fail(LTL_ERR_INVALID, "n_props must be in 1..32");
     if (max_size < 1 || max_size >= kMaxLevels) return fail(LTL_ERR_INVALID, "max_size must be in 1..63");
-    if (ops & ~(uint32_t)LTL_ALL) return fail(LTL_ERR_INVALID, "unknown connective bits in ops");
+    if (ops & ~(uint32_t)(LTL_ALL | LTL_NNF)) return fail(LTL_ERR_INVALID, "unknown connective bits in ops");
     return LTL_OK;
 }
 

@@ -251,6 +251,8 @@ __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, 
             }
         }
         if (k == key) {
+            // relaxed admission: an equal key is a duplicate, whatever the matrix
+            if (pb.ruc != RUC_EXACT) return DEC_DUP;
             uint32_t v;
             unsigned long long spins = 0;
             while ((v = ld_acquire_u32(pb.hvals + h)) == kValPending) {
@@ -284,6 +286,46 @@ __device__ __forceinline__ void record_separator(const Problem &pb, int level, u
 __device__ __forceinline__ unsigned long long fp_key(uint64_t s) {
     const unsigned long long key = mix64(s);
     return key ? key : 1ull;
+}
+
+// Hash-table key and first slot of a candidate from its reduced fingerprint s.
+// Exact admission: the finalised NH sum (then a full compare on a match).
+// Relaxed admission (Section 5): a 63-bit key -- the finalised NH sum, or the
+// first-k-percent bits themselves -- with the masked-out bits zeroed; bit 63
+// is set so that no key is 0 (the empty slot) and key equality is exactly
+// equality of the 63-bit values; the slot comes from a finalised copy.
+__device__ __forceinline__ unsigned long long admission_key(const Problem &pb, uint64_t s, unsigned long long &h) {
+    if (pb.ruc == RUC_EXACT) {
+        const unsigned long long key = fp_key(s);
+        h = key & pb.hmask;
+        return key;
+    }
+    const uint64_t v = (pb.ruc == RUC_HASH ? mix64(s) : s) & pb.key_mask;
+    const unsigned long long key = v | (1ull << 63);
+    h = mix64(key) & pb.hmask;
+    return key;
+}
+
+// First-k-percent term of one word of plane 0: the first b positions of trace
+// t go to bits [t*b, t*b + b) of the 63-bit key; what falls beyond bit 62 is
+// dropped.  Terms of different traces do not overlap, so summing them (the
+// reduction used for fingerprints) concatenates them.
+__device__ __forceinline__ uint64_t fkp_term(uint64_t positions, uint64_t t, uint32_t b) {
+    const uint64_t lo = t * (uint64_t)b;
+    if (lo >= 63) return 0;
+    const uint64_t v = b >= 64 ? positions : positions & ((1ull << b) - 1);
+    return (v << lo) & kKey63;
+}
+
+// First-k-percent terms of the 2x2 words (c, j) of a thread's fragment: word
+// (c, j) of plane 0 holds trace toff + c*cs + j (wide layout) or traces
+// 2(toff + c*cs + j) and 2(toff + c*cs + j) + 1 in its low and high halves
+// (narrow layout).
+template <bool NARROW>
+__device__ __forceinline__ uint64_t fkp_word(uint64_t w0, uint64_t word_index, uint32_t b) {
+    if (NARROW)
+        return fkp_term(w0 & 0xFFFFFFFFull, 2 * word_index, b) + fkp_term(w0 >> 32, 2 * word_index + 1, b);
+    return fkp_term(w0, word_index, b);
 }
 
 // Decodes tile k of a segment into operand ranges [a0, a1) x [b0, b1).

@@ -67,7 +67,7 @@ enum : int { S_PROBE = 0, S_STORE = 1, S_CMP = 2, S_DONE = 3 };
 template <int NB>
 struct FusedShared {
     unsigned long long fp[32][NB];
-    uint32_t bad[32];
+    uint32_t err[32][NB];
     unsigned long long tile;
     int skip;
     unsigned long long idx[2][NB];
@@ -158,10 +158,11 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
         constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
         Frag<W, C> r[NB];
         uint64_t fp[NB];
-        uint32_t badm = 0;
+        uint32_t errs[NB];
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             fp[k] = 0;
+            errs[k] = 0;
             if (k < nb) {
                 Frag<W, C> x, m;
                 load_frag<W, C, false>(slots + (uint64_t)(BIN ? NB : k) * lc.stride, lc.plane, lc.toff, lc.cs, x);
@@ -169,30 +170,43 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
                 if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
                 apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps);
                 const uint32_t bits = pos0_bits<W, C, NARROW>(r[k]);
-                badm |= (((bits ^ lc.want) & lc.care) != 0u ? 1u : 0u) << k;
+                errs[k] = (uint32_t)__popc((bits ^ lc.want) & lc.care);   // misclassified traces
             }
         }
+        if (pb.ruc != RUC_FKP) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
+            for (int c = 0; c < C; ++c) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const ulonglong2 key =
-                    __ldg(reinterpret_cast<const ulonglong2 *>(pb.keys + (uint64_t)w * lc.plane + lc.toff + c * lc.cs));
+                for (int w = 0; w < W; ++w) {
+                    const ulonglong2 key = __ldg(
+                        reinterpret_cast<const ulonglong2 *>(pb.keys + (uint64_t)w * lc.plane + lc.toff + c * lc.cs));
 #pragma unroll
-                for (int k = 0; k < NB; ++k)
-                    if (k < nb) fp[k] += nh_term(r[k].v[c][0][w], key.x) + nh_term(r[k].v[c][1][w], key.y);
+                    for (int k = 0; k < NB; ++k)
+                        if (k < nb) fp[k] += nh_term(r[k].v[c][0][w], key.x) + nh_term(r[k].v[c][1][w], key.y);
+                }
             }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+                        if (k < nb) fp[k] += fkp_word<NARROW>(r[k].v[c][j][0], lc.toff + c * lc.cs + j, pb.fkp_b);
         }
         // ---- 3. CTA reduction (also frees the operand slots)
 #pragma unroll
         for (int k = 0; k < NB; ++k)
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], off);
-        badm = __reduce_or_sync(0xffffffffu, badm);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) errs[k] = __reduce_add_sync(0xffffffffu, errs[k]);
         if (lc.lane == 0) {
 #pragma unroll
-            for (int k = 0; k < NB; ++k) sh.fp[lc.warp][k] = fp[k];
-            sh.bad[lc.warp] = badm;
+            for (int k = 0; k < NB; ++k) {
+                sh.fp[lc.warp][k] = fp[k];
+                sh.err[lc.warp][k] = errs[k];
+            }
         }
         __syncthreads();
         const uint64_t cur_a = a, cur_bf = bf;
@@ -206,16 +220,15 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
         uint64_t prov = 0;
         if (lc.warp == 0 && lc.lane < cur_nb) {
             uint64_t s = 0;
-            uint32_t bad = 0;
+            uint32_t nerr = 0;
             for (int w2 = 0; w2 < lc.nwarps; ++w2) {
                 s += sh.fp[w2][lc.lane];
-                bad |= sh.bad[w2];
+                nerr += sh.err[w2][lc.lane];
             }
             if (BIN) prov = prov_pack(OP, sg.a_begin + cur_a, sg.b_begin + cur_bf + lc.lane);
             else prov = prov_pack(OP, sg.a_begin + cur_a + lc.lane, 0);
-            if (!((bad >> lc.lane) & 1u)) record_separator(pb, level, prov);
-            key = fp_key(s);
-            h = key & pb.hmask;
+            if (nerr <= pb.max_errors) record_separator(pb, level, prov);   // eq. (dagger), or noisy
+            key = admission_key(pb, s, h);
             state = S_PROBE;
         }
         for (;;) {

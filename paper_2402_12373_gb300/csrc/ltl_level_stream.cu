@@ -14,7 +14,7 @@ namespace {
 
 struct StreamShared {
     unsigned long long fp[32];
-    int bad[32];
+    uint32_t err[32];
     unsigned long long tile;
     int skip;
     unsigned long long idx;
@@ -44,47 +44,53 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
     const uint64_t cs = 2ull * (uint64_t)NT;
     Frag<W, C> r;
     uint64_t fp = 0;
-    bool bad = false;
+    uint32_t nerr = 0;
     for (uint32_t g = 0; g < G; ++g) {
         const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
         stream_compute<OP, W, C>(pb, A, B, toff, cs, r);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
+            if (pb.ruc != RUC_FKP) {
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const ulonglong2 k =
-                    __ldg(reinterpret_cast<const ulonglong2 *>(pb.keys + (uint64_t)w * pb.plane + toff + c * cs));
-                fp += nh_term(r.v[c][0][w], k.x) + nh_term(r.v[c][1][w], k.y);
+                for (int w = 0; w < W; ++w) {
+                    const ulonglong2 k =
+                        __ldg(reinterpret_cast<const ulonglong2 *>(pb.keys + (uint64_t)w * pb.plane + toff + c * cs));
+                    fp += nh_term(r.v[c][0][w], k.x) + nh_term(r.v[c][1][w], k.y);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) fp += fkp_word<false>(r.v[c][j][0], toff + c * cs + j, pb.fkp_b);
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const uint64_t t = toff + c * cs + (uint64_t)j;
                 const bool v = (r.v[c][j][0] & 1ull) != 0;
-                bad |= (t < pb.n_traces) && (v != (t < pb.n_pos));
+                nerr += ((t < pb.n_traces) && (v != (t < pb.n_pos))) ? 1u : 0u;
             }
         }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) fp += __shfl_xor_sync(0xffffffffu, fp, off);
-    bad = __any_sync(0xffffffffu, bad);
+    nerr = __reduce_add_sync(0xffffffffu, nerr);
     const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0) {
         sh.fp[warp] = fp;
-        sh.bad[warp] = bad;
+        sh.err[warp] = nerr;
     }
     __syncthreads();
     const uint64_t prov = prov_pack(OP, a, BIN ? b : 0);
     unsigned long long key = 0;
     if (tid == 0) {
         uint64_t s = 0;
-        int anybad = 0;
+        uint32_t total_err = 0;
         for (int w2 = 0; w2 < (NT >> 5); ++w2) {
             s += sh.fp[w2];
-            anybad |= sh.bad[w2];
+            total_err += sh.err[w2];
         }
-        if (!anybad) record_separator(pb, level, prov);
-        key = fp_key(s);
-        sh.h = key & pb.hmask;
+        if (total_err <= pb.max_errors) record_separator(pb, level, prov);   // eq. (dagger), or noisy
+        unsigned long long h0 = 0;
+        key = admission_key(pb, s, h0);
+        sh.h = h0;
     }
     for (;;) {
         if (tid == 0) {

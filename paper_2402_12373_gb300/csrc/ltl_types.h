@@ -12,6 +12,10 @@ constexpr uint32_t kValPending = 0xFFFFFFFFu;   // slot claimed, entry not yet p
 constexpr uint32_t kValFail = 0xFFFFFFFEu;      // slot claimed but the cache was full
 constexpr uint64_t kMaxEntries = (1ull << 30) - 1;
 
+// Cache admission policies (relaxed uniqueness checks, Section 5).
+enum Ruc : uint32_t { RUC_EXACT = 0, RUC_HASH = 1, RUC_FKP = 2 };
+constexpr uint64_t kKey63 = (1ull << 63) - 1;   // relaxed admission keys have 63 bits
+
 // Provenance of a cache entry, packed: op in bits 60..62, left operand (or the
 // proposition index of an atom) in bits 30..59, right operand in bits 0..29.
 __host__ __device__ inline uint64_t prov_pack(int op, uint64_t a, uint64_t b) {
@@ -83,7 +87,10 @@ struct Problem {
     int32_t nsteps;               // log-step count: ceil(log2(max length))
     int32_t stop_first;           // stop at the first separator
     uint32_t groups;              // chunk groups per matrix (1: kept in registers)
-    uint32_t pad0;
+    uint32_t max_errors;          // misclassified traces a separator may have
+    uint32_t ruc;                 // admission policy: RUC_EXACT, RUC_HASH, RUC_FKP
+    uint32_t fkp_b;               // RUC_FKP: leading positions taken per trace
+    uint64_t key_mask;            // relaxed modes: admission-key bits kept (63 or fewer)
     unsigned long long spin_limit;
 };
 
