@@ -126,9 +126,11 @@ def profiled_traffic(sha):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms; only the
+    samples whose timestamps fall inside the timed region (mark_start /
+    mark_end) are summarised."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -136,15 +138,27 @@ class ClockSampler:
         self.idx = gpu_index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            # wait for the first sample, so that sampling covers the timed region
+            t_end = time.time() + 5.0
+            while time.time() < t_end and os.path.getsize(self.f.name) == 0:
+                time.sleep(0.02)
         except Exception:
             self.p = None
         return self
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+        time.sleep(0.12)   # let the sample that covers the end arrive
 
     def __exit__(self, *a):
         if self.p is not None:
@@ -155,6 +169,7 @@ class ClockSampler:
                 self.p.kill()
 
     def summary(self):
+        import datetime
         self.f.flush()
         self.f.seek(0)
         rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
@@ -164,17 +179,20 @@ class ClockSampler:
         for r in rows:
             r = [x.strip() for x in r]
             try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if self.t0 is not None and not (self.t0 - 0.05 <= ts <= self.t1 + 0.05):
+                    continue
+                sm.append(float(r[2]))
+                mx.append(float(r[3]))
             except (ValueError, IndexError):
                 continue
-            for n, v in zip(names, r[5:9]):
+            for n, v in zip(names, r[6:10]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": 50}
 
 
 def cpu_baseline(target_s: float = 12.0, max_size: int = 6):
@@ -352,6 +370,28 @@ def bench_trace_scaling(L, ws, spec, steps=2):
             "entries": r["entries"], "max_entries": r["max_entries"]}
 
 
+def bench_dc(L, ws, specs, windows=(16, 64)):
+    """Divide and conquer on Hamming(B, l, delta) (Section 7's high-cost
+    workload): U-free NNF formulae, max size 6 per part; wall time per
+    specification with host buffers, formula size and split statistics."""
+    ops = (L.ALL & ~L.U) | L.NNF
+    rows = []
+    for spec in specs:
+        for mode, mname in ((L.DC_RANDOM, "random"), (L.DC_DETERMINISTIC, "deterministic")):
+            for win in windows:
+                t0 = time.perf_counter()
+                r = L.learn_dc(spec.P, spec.N, spec.n_props, ops=ops, max_size=6, mode=mode, window=win, seed=1,
+                               workspace=ws)
+                wall = 1e3 * (time.perf_counter() - t0)
+                rows.append({"spec": spec.name, "traces": spec.n_traces, "split": mname, "window": win,
+                             "status": r["status"], "wall_ms": wall, "formula_size": r["formula_size"],
+                             "enum_calls": r["enum_calls"], "enum_failed": r["enum_failed"],
+                             "fallbacks": r["fallbacks"], "rounds": r["rounds"], "evals": r["evals"],
+                             "max_depth": r["max_depth"]})
+    return {"workload": "Hamming(B, l, delta): P = one random trace of length l over 2 propositions, N = all "
+                        "traces at bit distance delta; U-free NNF, max size 6 per part", "runs": rows}
+
+
 def run_reference(args):
     from paper_2402_12373_gb300 import dist
     rank, _, world = dist.env_rank()
@@ -386,7 +426,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-size", type=int, default=MAX_SIZE)
@@ -458,6 +498,7 @@ def main():
     with ClockSampler(gpu_idx) as clk:
         dist.barrier()
         torch.cuda.synchronize()
+        clk.mark_start()
         for _ in range(args.steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -469,6 +510,7 @@ def main():
             times.append(e0.elapsed_time(e1))
             results.append(r)
         torch.cuda.synchronize()
+        clk.mark_end()
         dist.barrier()
     clocks = clk.summary()
 
@@ -553,6 +595,7 @@ def main():
             out["batched"] = bench_batched(L, ws, extra[0])
             out["served"] = bench_served(L, ws, extra[1])
             out["trace_scaling"] = bench_trace_scaling(L, ws, extra[1][0])
+            out["divide_and_conquer"] = bench_dc(L, ws, [synth.hamming(24, 2, seed=1), synth.hamming(48, 2, seed=1)])
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))

@@ -332,6 +332,69 @@ ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_letters, cons
                             uint64_t n_traces, uint32_t max_len, int n_props, uint64_t *d_cs_out,
                             int words_per_trace, void *stream);
 
+/* -------------------------------------------------------------------------
+ * ltl_learn_dc -- divide and conquer over the enumerator (Section 6).
+ *
+ * A specification with more traces than the split window is split, each part
+ * of at most `window` traces is learned by the enumerator (all parts that are
+ * ready at once share launches, as in ltl_learn_batch), and the partial
+ * formulae are combined as (f11 & f12) | (f21 & f22).  The result separates
+ * (P, N) -- the call checks it on every trace before returning -- but is not
+ * minimal in general.
+ *   LTL_DC_DETERMINISTIC  detSplit: P and N halved in list order; f11 on
+ *                         (P1, N1), f12 on (P1, N2 accepted by f11), f21 on
+ *                         (P2 not accepted by f11 & f12, N1), f22 on (that
+ *                         P2, N2 accepted by f21), one after another.
+ *   LTL_DC_RANDOM         randSplit: f11 on a random balanced sample of at
+ *                         most `window` traces; then, concurrently, f12 on the
+ *                         traces f11 accepts, f21 on those it rejects, f22 on
+ *                         the positives it rejects against the negatives it
+ *                         accepts.
+ * A part the enumerator cannot solve within max_size or its memory budget is
+ * retried with half the window; a part of one positive and one negative trace
+ * that still fails is closed by a formula telling the two traces apart (their
+ * first differing position, or the end of the shorter one).
+ *
+ * Arguments as ltl_learn; ops must allow & and | (the combination uses them);
+ * opts->stop_on_solution is ignored (each part stops at its first
+ * separator); opts->max_errors must be 0; costs, NNF and relaxed admission
+ * apply to every part.  Results may vary between runs (which minimal formula
+ * a part returns depends on timing); with LTL_DC_RANDOM the samples are drawn
+ * from `seed`.  Traces may have at most 1024 positions.
+ * Returns LTL_OK with the formula; LTL_NOT_FOUND when no formula over the
+ * allowed connectives can separate (a trace in both P and N, an empty
+ * positive trace, or a positive trace that is a prefix of a negative one
+ * under LTL_NNF); LTL_ERR_BUFSIZE when formula_cap is too small
+ * (stats->formula_len holds the length).
+ * -------------------------------------------------------------------------*/
+enum { LTL_DC_DETERMINISTIC = 0, LTL_DC_RANDOM = 1 };
+
+typedef struct {
+    int mode;              /* LTL_DC_DETERMINISTIC or LTL_DC_RANDOM             */
+    uint64_t window;       /* split window: most traces (|P| + |N|) sent to one
+                              enumeration; at least 2                          */
+    uint64_t seed;         /* LTL_DC_RANDOM: seed of the sample draws          */
+    int max_resident;      /* parts enumerated concurrently; 0 = 64            */
+} ltl_dc_opts;
+
+typedef struct {
+    uint64_t enum_calls;   /* parts sent to the enumerator                    */
+    uint64_t enum_failed;  /* of which found no formula (window halved)       */
+    uint64_t fallbacks;    /* parts closed by a distinguishing formula        */
+    uint64_t evals;        /* formulae evaluated on all traces (membership)   */
+    uint64_t rounds;       /* enumeration rounds (shared launch groups)       */
+    uint64_t min_window;   /* smallest split window used                      */
+    int max_depth;         /* depth of the deepest part enumerated or split
+                              (0: the whole specification in one enumeration) */
+    uint64_t formula_size; /* syntax-tree nodes of the returned formula       */
+    uint64_t formula_len;  /* its text length, without the terminating NUL    */
+    double total_ms;
+} ltl_dc_stats;
+
+ltl_status ltl_learn_dc(const ltl_traces *P, const ltl_traces *N, int n_props, uint32_t ops, int max_size,
+                        const ltl_opts *opts, const ltl_dc_opts *dc, char *formula_out, size_t formula_cap,
+                        ltl_dc_stats *stats);
+
 /* Message of the last error on this host thread (static storage). */
 const char *ltl_last_error(void);
 

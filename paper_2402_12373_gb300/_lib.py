@@ -23,6 +23,7 @@ STATUS = {0: "found", 1: "not_found", 2: "cap", -1: "invalid", -2: "cuda", -3: "
 NOT, AND, OR, X, F, G, U, ALL = 1, 2, 4, 8, 16, 32, 64, 127
 NNF = 256   # negation on atoms only (flag in the ops mask)
 RUC_EXACT, RUC_HASH, RUC_FKP = 0, 1, 2   # cache admission policies
+DC_DETERMINISTIC, DC_RANDOM = 0, 1       # divide-and-conquer split modes
 STOP_NONE, STOP_FIRST, STOP_LEVEL = 0, 1, 2
 MAX_LEVELS = 64
 
@@ -30,7 +31,7 @@ MAX_LEVELS = 64
 EXPORTS = ["ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_destroy", "ltl_ctx_learn",
            "ltl_ctx_learn_device", "ltl_ctx_level_range", "ltl_ctx_entry", "ltl_last_error",
            "ltl_version", "ltl_eval_noalloc", "ltl_learn_batch", "ltl_server_create", "ltl_ctx_set_mem_budget",
-           "ltl_server_submit", "ltl_server_poll", "ltl_server_pending", "ltl_server_destroy"]
+           "ltl_server_submit", "ltl_server_poll", "ltl_server_pending", "ltl_server_destroy", "ltl_learn_dc"]
 FORMULA_MAX = 512
 
 
@@ -158,6 +159,9 @@ def load(build_if_missing: bool = True):
     L.ltl_server_pending.restype = ctypes.c_int
     L.ltl_server_destroy.argtypes = [vp]
     L.ltl_server_destroy.restype = None
+    L.ltl_learn_dc.argtypes = [TP, TP, i32, u32, i32, ctypes.POINTER(Opts), ctypes.POINTER(DcOpts), ctypes.c_char_p,
+                               ctypes.c_size_t, ctypes.POINTER(DcStats)]
+    L.ltl_learn_dc.restype = ctypes.c_int
     L.ltl_last_error.restype = ctypes.c_char_p
     L.ltl_version.restype = ctypes.c_char_p
     for f in ("ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_learn", "ltl_ctx_learn_device",
@@ -429,6 +433,47 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+class DcOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("window", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("max_resident", ctypes.c_int)]
+
+
+class DcStats(ctypes.Structure):
+    _fields_ = [("enum_calls", ctypes.c_uint64), ("enum_failed", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64),
+                ("evals", ctypes.c_uint64), ("rounds", ctypes.c_uint64), ("min_window", ctypes.c_uint64),
+                ("max_depth", ctypes.c_int), ("formula_size", ctypes.c_uint64), ("formula_len", ctypes.c_uint64),
+                ("total_ms", ctypes.c_double)]
+
+    def to_dict(self) -> Dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def learn_dc(P, N, n_props: int, ops: int = ALL, max_size: int = 7, mode: int = DC_RANDOM, window: int = 64,
+             seed: int = 0, max_resident: int = 0, workspace=None, mem_budget: int = 0, costs=None,
+             ruc: int = RUC_EXACT, ruc_mask_bits: int = 0) -> Dict:
+    """ltl_learn_dc: divide and conquer over the enumerator (host traces).
+    Returns the formula, the status and the split statistics."""
+    L = load()
+    hp, hn = _HostTraces(P), _HostTraces(N)
+    o = _opts(STOP_FIRST, workspace, _current_stream() if workspace is not None else None, mem_budget, 0, 0, costs,
+              0, ruc, ruc_mask_bits)
+    dc = DcOpts(int(mode), int(window), int(seed), int(max_resident))
+    st = DcStats()
+    cap = 1 << 16
+    for _ in range(2):
+        buf = ctypes.create_string_buffer(cap)
+        rc = L.ltl_learn_dc(ctypes.byref(hp.struct), ctypes.byref(hn.struct), n_props, ops, max_size,
+                            ctypes.byref(o), ctypes.byref(dc), buf, len(buf), ctypes.byref(st))
+        if rc != LTL_ERR_BUFSIZE:
+            break
+        cap = int(st.formula_len) + 1
+    _check(rc)
+    d = st.to_dict()
+    d["status"] = STATUS[rc]
+    d["formula"] = buf.value.decode() if rc == LTL_OK else None
+    return d
 
 
 def version() -> str:

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -950,6 +951,82 @@ ltl_status run_single(Engine &e, ProblemIn &&in, char *formula_out, size_t formu
     return sl.status;
 }
 
+// ============================================================= BatchRunner
+
+struct BatchRunner {
+    Engine e;
+    std::deque<ProblemIn> queue;
+    uint64_t share = 0;
+};
+
+ltl_status runner_create(const ltl_opts &o, int max_resident, int share_divisor, BatchRunner **out) {
+    *out = nullptr;
+    std::unique_ptr<BatchRunner> r(new BatchRunner());
+    ltl_status s = r->e.setup(&o, max_resident, false);
+    if (s != LTL_OK) return s;
+    s = r->e.ensure_workspace(r->e.shared_end + ((size_t)64 << 20));
+    if (s != LTL_OK) return s;
+    r->share = (r->e.ws_bytes - r->e.shared_end) / (uint64_t)std::max(1, share_divisor);
+    *out = r.release();
+    return LTL_OK;
+}
+
+void runner_destroy(BatchRunner *r) { delete r; }
+
+ltl_status runner_submit(BatchRunner *r, const ltl_traces &P, const ltl_traces &N, int n_props, uint32_t ops,
+                         int max_size, uint64_t budget, uint64_t id, bool copy) {
+    ProblemIn in;
+    ltl_status s = problem_from_host(&P, &N, n_props, ops, max_size, budget, copy, in);
+    if (s != LTL_OK) return s;
+    in.id = id;
+    r->queue.push_back(std::move(in));
+    return LTL_OK;
+}
+
+ltl_status runner_step(BatchRunner *r, std::vector<ltl_result> &done) {
+    Engine &e = r->e;
+    // admit in order while memory and slots allow
+    while (!r->queue.empty()) {
+        int si = -1;
+        for (int j = 0; j < e.max_slots; ++j)
+            if (e.slots[j].state == SLOT_FREE) {
+                si = j;
+                break;
+            }
+        if (si < 0) break;
+        ProblemIn &front = r->queue.front();
+        const uint64_t budget = front.budget ? front.budget : r->share;
+        const ltl_status as = e.admit(si, front, budget);
+        if (as == LTL_OK) {
+            r->queue.pop_front();
+            continue;
+        }
+        if (as == LTL_ERR_OOM && e.resident() > 0) break;   // wait for memory
+        ltl_result res;                                     // does not fit even alone, or invalid
+        memset(&res, 0, sizeof res);
+        res.id = front.id;
+        res.status = as;
+        done.push_back(res);
+        r->queue.pop_front();
+    }
+    if (e.resident() == 0) return LTL_OK;
+    ltl_status s = e.round();
+    if (s != LTL_OK) return s;
+    for (int j = 0; j < e.max_slots; ++j) {
+        Slot &sl = e.slots[j];
+        if (sl.state != SLOT_DONE) continue;
+        ltl_result res;
+        e.fill_result(sl, res);
+        done.push_back(res);
+        e.release(j);
+    }
+    return LTL_OK;
+}
+
+bool runner_busy(const BatchRunner *r) { return !r->queue.empty() || r->e.resident() > 0; }
+cudaStream_t runner_stream(const BatchRunner *r) { return r->e.stream; }
+uint64_t runner_rounds(const BatchRunner *r) { return r->e.total_rounds; }
+
 }  // namespace ltl
 
 using namespace ltl;
@@ -1090,58 +1167,25 @@ ltl_status ltl_learn_batch(int n, const ltl_problem *problems, const ltl_opts *o
     const ltl_opts o = opts ? *opts : default_opts();
     if (o.stop_on_solution < 0 || o.stop_on_solution > 2) return fail(LTL_ERR_INVALID, "stop_on_solution must be 0, 1 or 2");
     const int resident_cap = std::min(n, 1024);
-    Engine e;
-    ltl_status s = e.setup(&o, resident_cap, false);
+    BatchRunner *r = nullptr;
+    ltl_status s = runner_create(o, resident_cap, resident_cap, &r);
     if (s != LTL_OK) return s;
+    std::unique_ptr<BatchRunner, void (*)(BatchRunner *)> guard(r, runner_destroy);
     // problems are queued in input order; each needs its budget (or an equal
     // share of the workspace) of contiguous memory to be admitted
-    std::deque<int> queue;
-    std::vector<ProblemIn> ins(n);
     for (int i = 0; i < n; ++i) {
         const ltl_problem &p = problems[i];
-        s = problem_from_host(&p.P, &p.N, p.n_props, p.ops, p.max_size, p.mem_budget_bytes, false, ins[i]);
         memset(&out[i], 0, sizeof(ltl_result));
         out[i].id = (uint64_t)i;
-        if (s != LTL_OK) {
-            out[i].status = s;
-            continue;
-        }
-        ins[i].id = (uint64_t)i;
-        queue.push_back(i);
+        s = runner_submit(r, p.P, p.N, p.n_props, p.ops, p.max_size, p.mem_budget_bytes, (uint64_t)i, false);
+        if (s != LTL_OK) out[i].status = s;
     }
-    s = e.ensure_workspace(e.shared_end + ((size_t)64 << 20));
-    if (s != LTL_OK) return s;
-    const uint64_t share = (e.ws_bytes - e.shared_end) / (uint64_t)std::max(1, std::min<int>(n, resident_cap));
-    while (!queue.empty() || e.resident() > 0) {
-        // admit in order while memory and slots allow
-        while (!queue.empty()) {
-            int si = -1;
-            for (int j = 0; j < e.max_slots; ++j)
-                if (e.slots[j].state == SLOT_FREE) {
-                    si = j;
-                    break;
-                }
-            if (si < 0) break;
-            const int pi = queue.front();
-            const uint64_t budget = ins[pi].budget ? ins[pi].budget : share;
-            ltl_status as = e.admit(si, ins[pi], budget);
-            if (as == LTL_OK) {
-                queue.pop_front();
-                continue;
-            }
-            if (as == LTL_ERR_OOM && e.resident() > 0) break;   // wait for memory
-            out[pi].status = as;   // does not fit even alone, or invalid
-            queue.pop_front();
-        }
-        if (e.resident() == 0) continue;
-        s = e.round();
+    std::vector<ltl_result> done;
+    while (runner_busy(r)) {
+        s = runner_step(r, done);
         if (s != LTL_OK) return s;
-        for (int j = 0; j < e.max_slots; ++j) {
-            Slot &sl = e.slots[j];
-            if (sl.state != SLOT_DONE) continue;
-            e.fill_result(sl, out[sl.in.id]);
-            e.release(j);
-        }
+        for (const ltl_result &d : done) out[d.id] = d;
+        done.clear();
     }
     return LTL_OK;
 }

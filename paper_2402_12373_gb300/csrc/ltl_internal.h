@@ -47,6 +47,25 @@ ltl_status check_common(int n_props, uint32_t ops, int max_size);
 ltl_status check_traces(const ltl_traces *t, const char *name);
 uint64_t traces_max_len(const ltl_traces *t);
 
+// ---- batch runner: an engine that advances queued learning problems one
+// level per round, with launches shared between the resident problems
+// (continuous batching; used by ltl_learn_batch and divide and conquer)
+struct BatchRunner;
+// `share_divisor`: a problem without its own budget gets this fraction of the
+// workspace left after the shared region
+ltl_status runner_create(const ltl_opts &o, int max_resident, int share_divisor, BatchRunner **out);
+void runner_destroy(BatchRunner *r);
+// queues a problem; the traces are copied when `copy`, else they must stay
+// valid until its result comes back; `id` comes back in its result
+ltl_status runner_submit(BatchRunner *r, const ltl_traces &P, const ltl_traces &N, int n_props, uint32_t ops,
+                         int max_size, uint64_t budget, uint64_t id, bool copy);
+// admits queued problems while slots and memory allow, runs one round, and
+// appends the results of the problems that finished (or could not be admitted)
+ltl_status runner_step(BatchRunner *r, std::vector<ltl_result> &done);
+bool runner_busy(const BatchRunner *r);
+cudaStream_t runner_stream(const BatchRunner *r);
+uint64_t runner_rounds(const BatchRunner *r);
+
 // ---- kernels (device code lives in the other translation units)
 const void *fused_kernel_ptr_w1(int C, int op);
 const void *fused_kernel_ptr_w2(int C, int op);

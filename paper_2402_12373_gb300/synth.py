@@ -37,6 +37,7 @@ by a separating formula):
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 from typing import List, Optional, Sequence, Tuple
 
@@ -421,3 +422,24 @@ def random_small(seed: int, n_traces: int, n_props: int, lo: int, hi: int,
     return Spec(TraceSet.from_dense(bits[:h], lens[:h]),
                 TraceSet.from_dense(bits[h:], lens[h:]), n_props, None, None,
                 "random_small_%d" % seed)
+
+
+def hamming(l: int, delta: int, n_props: int = 2, seed: int = 0) -> Spec:
+    """Hamming(B, l, delta) of Section 7: P = {tr} with tr uniform among the
+    traces of length l (each position a letter of n_props propositions, one
+    fair bit each), N = every trace of length l whose bits differ from tr's in
+    exactly delta places (|N| = C(l * n_props, delta); with 2 propositions and
+    l = 48, delta = 2 that is 4560)."""
+    if l < 1 or delta < 1 or delta > l * n_props:
+        raise ValueError("need 1 <= delta <= l * n_props")
+    u = splitmix64(np.uint64(seed), _AUX_COUNTER + np.uint64(1 << 20) + np.arange(l * n_props, dtype=np.uint64))
+    bits = (u >> np.uint64(63)).astype(np.uint32)          # one fair bit per (position, proposition)
+    tr = [int(sum(int(bits[i * n_props + q]) << q for q in range(n_props))) for i in range(l)]
+    neg = []
+    for flips in itertools.combinations(range(l * n_props), delta):
+        t = list(tr)
+        for b in flips:
+            t[b // n_props] ^= 1 << (b % n_props)
+        neg.append(t)
+    return Spec(TraceSet.from_list([tr]), TraceSet.from_list(neg), n_props, None, None,
+                "hamming_%d_%d" % (l, delta))

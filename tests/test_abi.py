@@ -64,6 +64,11 @@ def test_host_side_validation_without_gpu():
         _lib.evaluate("p0", bad, 2)
     assert e.value.status == _lib.LTL_ERR_INVALID
     assert "decrease" in _lib.last_error()
+    # divide and conquer: window, split mode and connectives are checked first
+    for kw in (dict(window=1), dict(mode=7), dict(ops=_lib.ALL & ~_lib.OR)):
+        with pytest.raises(_lib.LtlError) as e:
+            _lib.learn_dc(ts, ts, 2, **kw)
+        assert e.value.status == _lib.LTL_ERR_INVALID
 
 
 def _files(d, exts):
