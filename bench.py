@@ -435,6 +435,8 @@ def main():
                     help="skip the batched, served and trace-scaling measurements")
     ap.add_argument("--max-chunks", type=int, default=0,
                     help="launch-shape cap (16-byte chunks per thread); 0 = automatic")
+    ap.add_argument("--level-kernel", default="auto", choices=["auto", "fused", "ws"],
+                    help="size-level kernel: automatic choice, fused, or warp-specialised")
     ap.add_argument("--ws-gb", type=float, default=0.0,
                     help="workspace size in GB (default: half of the free device memory)")
     args = ap.parse_args()
@@ -476,6 +478,7 @@ def main():
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    L.DEFAULT_LEVEL_KERNEL = {"auto": L.KERNEL_AUTO, "fused": L.KERNEL_FUSED, "ws": L.KERNEL_WS}[args.level_kernel]
     ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks)
 
     def step():

@@ -130,7 +130,21 @@ typedef struct {
     uint32_t ruc_mask_bits;      /* relaxed modes: zero this many of the 63
                                     admission-key bits, the highest first
                                     (0..62; the masking experiment, Sec. 7)   */
+    uint32_t level_kernel;       /* LTL_KERNEL_*: which size-level kernel runs
+                                    matrices that fit one CTA                 */
 } ltl_opts;
+
+/* level_kernel values.  Both kernels compute the same candidates, counts and
+ * cache; they differ in how the check-and-cache step is scheduled.
+ *   LTL_KERNEL_AUTO   the fused kernel (default; on the workloads measured the
+ *                     two run at the same speed and the fused one needs less
+ *                     shared memory)
+ *   LTL_KERNEL_FUSED  all warps compute a batch, then probe and store it
+ *   LTL_KERNEL_WS     compute warps hand each batch to dedicated hash warps
+ *                     through a shared-memory ring and compute the next one
+ *                     while it is probed (when the ring fits in shared
+ *                     memory; else the fused kernel) */
+enum { LTL_KERNEL_AUTO = 0, LTL_KERNEL_FUSED = 1, LTL_KERNEL_WS = 2 };
 
 #define LTL_MAX_LEVELS 64
 
@@ -158,7 +172,10 @@ typedef struct {
     float op_ms[LTL_MAX_LEVELS][8];       /* device time of each connective's
                                              launch: [level][op], op = 0 atoms,
                                              1 Not, 2 And, 3 Or, 4 X, 5 F, 6 G,
-                                             7 U                               */
+                                             7 U.  Levels of fewer than 2^17
+                                             candidates run their launches
+                                             concurrently; there it is the time
+                                             from the level's start           */
 } ltl_stats;
 
 /* ---------------------------------------------------------------------------

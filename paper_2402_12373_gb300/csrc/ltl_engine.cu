@@ -32,11 +32,20 @@ namespace {
 constexpr uint64_t kKeySeed = 0x243F6A8885A308D3ull;   // NH key stream seed (digits of pi)
 constexpr int kMaxTokens = 256;
 constexpr int kMaxGroups = 512;                       // launches per round
+// Rounds with fewer candidates than this run their launches concurrently on
+// auxiliary streams: small levels are launch-latency bound, and the
+// connectives of a level are independent (they meet only in the lock-free
+// hash set).  Larger rounds run their launches one after another, so each
+// launch's time is its own.
+constexpr uint64_t kConcurrentBelow = 1ull << 17;
+constexpr int kAuxStreams = 8;
 
 // Where one problem's device state lives, relative to its region base.
 struct Layout {
     int W = 0, Wt = 0, C = 0, NT = 0, NB = 1;
+    int block = 0;          // threads per CTA: NT, plus the hash warps of the warp-specialised kernel
     bool narrow = false;
+    bool ws = false;        // warp-specialised level kernel
     uint32_t G = 0;
     uint32_t n_traces = 0, n_pos = 0;
     int n_props = 0, nsteps = 0;
@@ -129,7 +138,12 @@ struct FreeList {
 
 // Chooses the launch shape of a problem and carves its region for `budget`
 // bytes (0: as many entries as `avail` bytes allow).
-ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint64_t budget, uint64_t avail, Layout &L) {
+// Dynamic shared memory the warp-specialised kernel may take: what is left
+// of the opt-in maximum (227 KB) after its static part, rounded down.
+constexpr size_t kWsSmemMax = 224 * 1024;
+
+ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_kernel, uint64_t budget,
+                       uint64_t avail, Layout &L) {
     const uint64_t T = in.n_pos + in.n_neg;
     if (T > 0x7fffffffull) return fail(LTL_ERR_INVALID, "too many traces (%llu)", (unsigned long long)T);
     L = Layout{};
@@ -176,6 +190,17 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint64_t budget
     L.plane = (uint64_t)L.G * L.C * 2 * L.NT;   // words per bit-plane
     L.stride = (uint64_t)L.Wt * L.plane;
     L.smem = L.G == 1 ? (size_t)(L.NB + 1) * 8 * L.stride : 0;
+    L.block = L.NT;
+    // the warp-specialised kernel adds a ring of two batches of results
+    const size_t ws_smem = (size_t)(3 * L.NB + 1) * 8 * L.stride;
+    // on request, any shape whose ring fits; the automatic choice is the
+    // fused kernel (as fast on the measured workloads, less shared memory)
+    const bool want_ws = level_kernel == LTL_KERNEL_WS;
+    if (L.G == 1 && want_ws && ws_smem <= kWsSmemMax) {
+        L.ws = true;
+        L.smem = ws_smem;
+        L.block = L.NT + kWsExtraThreads;
+    }
 
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -349,6 +374,7 @@ public:
     }
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     std::vector<cudaEvent_t> ev_op;   // after each launch of a round, created on demand
+    std::vector<cudaStream_t> aux;    // concurrent launches of small rounds, created on demand
     uint64_t total_rounds = 0;
 
     ~Engine() { teardown(); }
@@ -357,6 +383,7 @@ public:
         opts = *o;
         if (opts.ruc > LTL_RUC_FKP) return fail(LTL_ERR_INVALID, "ruc must be LTL_RUC_EXACT, LTL_RUC_HASH or LTL_RUC_FKP");
         if (opts.ruc_mask_bits > 62) return fail(LTL_ERR_INVALID, "ruc_mask_bits must be at most 62");
+        if (opts.level_kernel > LTL_KERNEL_WS) return fail(LTL_ERR_INVALID, "level_kernel must be LTL_KERNEL_AUTO, _FUSED or _WS");
         keep_finished = keep;
         max_slots = std::max(1, std::min(max_resident, 4096));
         cudaError_t e = cudaGetDevice(&device);
@@ -425,6 +452,12 @@ public:
         for (auto &ev : ev_op)
             if (ev) cudaEventDestroy(ev);
         ev_op.clear();
+        for (auto &st : aux)
+            if (st) {
+                cudaStreamSynchronize(st);
+                cudaStreamDestroy(st);
+            }
+        aux.clear();
         if (own_stream && stream) cudaStreamDestroy(stream);
         stream = nullptr;
         (void)cudaGetLastError();
@@ -474,6 +507,10 @@ public:
     }
 
     const void *kernel_for(const Layout &L, int op) const {
+        if (L.ws) {
+            if (L.narrow) return ws_kernel_ptr_narrow(L.C, op);
+            return L.Wt == 1 ? ws_kernel_ptr_w1(L.C, op) : ws_kernel_ptr_wn(L.Wt, L.C, op);
+        }
         if (L.narrow) return fused_kernel_ptr_narrow(L.C, op);
         return L.G == 1 ? fused_kernel_ptr(L.Wt, L.C, op) : stream_kernel_ptr(L.Wt, L.C);
     }
@@ -517,7 +554,7 @@ public:
         Layout L;
         const uint64_t budget = in.budget ? in.budget : default_budget;
         const size_t avail = mem.largest();
-        ltl_status st = plan_layout(in, opts.max_chunks, budget, avail, L);
+        ltl_status st = plan_layout(in, opts.max_chunks, opts.level_kernel, budget, avail, L);
         if (st != LTL_OK) return st;
         size_t off = 0;
         if (!mem.alloc(L.end, off)) return fail(LTL_ERR_OOM, "no free device region of %zu bytes", L.end);
@@ -598,14 +635,14 @@ public:
                                      cudaMemcpyHostToDevice, stream));
         s.st.n_traces = T;
         s.st.words_per_trace = (uint32_t)L.W;
-        s.st.threads_per_cta = (uint32_t)L.NT;
+        s.st.threads_per_cta = (uint32_t)L.block;   // with the hash warps of the warp-specialised kernel
         s.st.traces_per_thread = (uint32_t)(L.narrow ? 4 * L.C : 2 * L.C);
         s.st.traces_per_word = L.narrow ? 2u : 1u;
         s.st.chunk_groups = L.G;
         s.st.batch = (uint32_t)L.NB;
         s.st.max_entries = L.max_entries;
         int bps = 0;
-        if (occupancy(kernel_for(L, OP_U), L.NT, L.smem, bps) == LTL_OK) s.st.ctas_per_sm = (uint32_t)bps;
+        if (occupancy(kernel_for(L, OP_U), L.block, L.smem, bps) == LTL_OK) s.st.ctas_per_sm = (uint32_t)bps;
         return LTL_OK;
     }
 
@@ -664,9 +701,9 @@ public:
             const void *fn = kernel_for(s.L, segs[i].op);
             int g = -1;
             for (int j = 0; j < (int)groups.size(); ++j)
-                if (groups[j].fn == fn && groups[j].nt == s.L.NT) g = j;
+                if (groups[j].fn == fn && groups[j].nt == s.L.block) g = j;
             if (g < 0) {
-                groups.push_back(Group{fn, s.L.NT, segs[i].op, s.L.NB, 0, {}});
+                groups.push_back(Group{fn, s.L.block, segs[i].op, s.L.NB, 0, {}});
                 g = (int)groups.size() - 1;
             }
             groups[g].smem = std::max(groups[g].smem, s.L.smem);
@@ -678,6 +715,7 @@ public:
         std::vector<size_t> first(groups.size());
         std::vector<uint64_t> tiles(groups.size());
         std::vector<int> grid(groups.size());
+        uint64_t round_cands = 0;
         for (size_t g = 0; g < groups.size(); ++g) {
             Group &gr = groups[g];
             int bps = 0;
@@ -686,6 +724,7 @@ public:
             const uint64_t cap = (uint64_t)bps * (uint64_t)n_sm;
             uint64_t cands = 0;
             for (int i : gr.seg_ids) cands += seg_candidates(segs[i]);
+            round_cands += cands;
             const uint32_t cpt = tile_target(cands, cap, gr.nb);
             uint64_t total = 0;
             first[g] = n_out;
@@ -709,6 +748,13 @@ public:
         LTL_CUDA_TRY(cudaMemcpyAsync(d_segs, h_segs, sizeof(Seg) * n_out, cudaMemcpyHostToDevice, stream));
         LTL_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * groups.size(), stream));
         LTL_CUDA_TRY(cudaEventRecord(ev_begin, stream));
+        const bool concurrent = groups.size() > 1 && round_cands < kConcurrentBelow;
+        if (concurrent)
+            while ((int)aux.size() < kAuxStreams) {
+                cudaStream_t st = nullptr;
+                LTL_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+                aux.push_back(st);
+            }
         for (size_t g = 0; g < groups.size(); ++g) {
             LevelArgs la{};
             la.segs = d_segs + first[g];
@@ -717,23 +763,33 @@ public:
             la.n_segs = (int)groups[g].seg_ids.size();
             la.total_tiles = tiles[g];
             void *args[] = {&la};
+            cudaStream_t st = stream;
+            if (concurrent) {
+                st = aux[g % aux.size()];
+                LTL_CUDA_TRY(cudaStreamWaitEvent(st, ev_begin, 0));
+            }
             if (grid[g] > 0)
-                LTL_CUDA_TRY(cudaLaunchKernel(groups[g].fn, dim3(grid[g]), dim3(groups[g].nt), args, groups[g].smem,
-                                              stream));
-            LTL_CUDA_TRY(cudaEventRecord(ev_op[g], stream));
+                LTL_CUDA_TRY(cudaLaunchKernel(groups[g].fn, dim3(grid[g]), dim3(groups[g].nt), args, groups[g].smem, st));
+            LTL_CUDA_TRY(cudaEventRecord(ev_op[g], st));
         }
+        if (concurrent)
+            for (size_t g = 0; g < groups.size(); ++g) LTL_CUDA_TRY(cudaStreamWaitEvent(stream, ev_op[g], 0));
         int hi = 0;
         for (int si : ran) hi = std::max(hi, si + 1);
         LTL_CUDA_TRY(cudaMemcpyAsync(h_ctrls, ws + o_ctrls, sizeof(Ctrl) * hi, cudaMemcpyDeviceToHost, stream));
         LTL_CUDA_TRY(cudaStreamSynchronize(stream));
         ++total_rounds;
+        // per launch: its own time when launches ran one after another; from
+        // the start of the round when they ran concurrently
         float round_ms = 0.f;
-        LTL_CUDA_TRY(cudaEventElapsedTime(&round_ms, ev_begin, ev_op[groups.size() - 1]));
         std::vector<float> op_ms(groups.size());
         for (size_t g = 0; g < groups.size(); ++g) {
             float t = 0.f;
-            LTL_CUDA_TRY(cudaEventElapsedTime(&t, g == 0 ? ev_begin : ev_op[g - 1], ev_op[g]));
+            LTL_CUDA_TRY(cudaEventElapsedTime(&t, (g == 0 || concurrent) ? ev_begin : ev_op[g - 1], ev_op[g]));
             op_ms[g] = t;
+            float since = 0.f;
+            LTL_CUDA_TRY(cudaEventElapsedTime(&since, ev_begin, ev_op[g]));
+            round_ms = std::max(round_ms, since);
         }
         // close the level of every problem that ran
         std::vector<int> found_slots;
@@ -927,7 +983,7 @@ ltl_status run_single(Engine &e, ProblemIn &&in, char *formula_out, size_t formu
     if (e.slots[0].state != SLOT_FREE) e.release(0);
     // size the workspace for this problem's fixed part (and let it grow)
     Layout probe;
-    ltl_status s = plan_layout(in, e.opts.max_chunks, 0, (uint64_t)1 << 62, probe);
+    ltl_status s = plan_layout(in, e.opts.max_chunks, e.opts.level_kernel, 0, (uint64_t)1 << 62, probe);
     if (s != LTL_OK) return s;
     const size_t fixed = probe.o_hkeys + (1 << 20);
     s = e.ensure_workspace(e.shared_end + fixed + (e.opts.mem_budget_bytes ? e.opts.mem_budget_bytes : 0));
