@@ -533,6 +533,9 @@ public:
             LTL_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
             const int dyn = optin - (int)fa.sharedSizeBytes;
             LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+            // all of the unified L1 / shared storage as shared memory, so that
+            // shared memory does not cap the resident CTAs below the registers
+            LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             opted_in.push_back(fn);
         }
         if ((long long)smem > (long long)max_dynamic_smem(fn))
