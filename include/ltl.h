@@ -368,6 +368,8 @@ ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_letters, cons
  *                         the positives it rejects against the negatives it
  *                         accepts.
  * A part the enumerator cannot solve within max_size or its memory budget is
+ * closed by the overfitting formula of its positive trace when it has only
+ * one (Section 3's fallback: that trace's letters under nested X's), else
  * retried with half the window; a part of one positive and one negative trace
  * that still fails is closed by a formula telling the two traces apart (their
  * first differing position, or the end of the shorter one).
@@ -397,7 +399,8 @@ typedef struct {
 typedef struct {
     uint64_t enum_calls;   /* parts sent to the enumerator                    */
     uint64_t enum_failed;  /* of which found no formula (window halved)       */
-    uint64_t fallbacks;    /* parts closed by a distinguishing formula        */
+    uint64_t fallbacks;    /* parts closed by an overfitting or distinguishing
+                              formula                                         */
     uint64_t evals;        /* formulae evaluated on all traces (membership)   */
     uint64_t rounds;       /* enumeration rounds (shared launch groups)       */
     uint64_t min_window;   /* smallest split window used                      */

@@ -9,10 +9,11 @@
 // the earlier parts already decide; random splitting learns f11 on a random
 // balanced sample of at most `window` traces and then the three remaining
 // parts (independent of each other) concurrently.  When the enumerator finds
-// no formula within max_size or its memory, the window of that
-// sub-specification is halved; a sub-specification of one positive and one
-// negative trace that still fails is closed by a formula that distinguishes
-// the two traces (the overfitting fallback of Section 3).
+// no formula within max_size or its memory, a sub-specification with a single
+// positive trace is closed by that trace's overfitting formula (the fallback
+// of Section 3); otherwise its window is halved, and a sub-specification of
+// one positive and one negative trace that still fails is closed by a formula
+// that distinguishes the two traces.
 //
 // Every sub-specification that is ready is queued on one batch runner, so the
 // enumerations of independent parts share launches (continuous batching).
@@ -340,6 +341,15 @@ private:
         const uint64_t card = n.P0.size() + n.N0.size();
         if (r.status == LTL_OK) return learned(ni, f_text(r.formula));
         st.enum_failed++;
+        if (n.P.size() == 1) {
+            // one positive trace: its overfitting formula rejects every
+            // negative of the part at once (Section 3's fallback)
+            Fml f;
+            if (overfit(n.P[0], n.N, f)) {
+                st.fallbacks++;
+                return learned(ni, f);
+            }
+        }
         if (card <= 2) {
             // one positive, one negative: the distinguishing formula
             Fml f;
@@ -431,6 +441,47 @@ private:
         default:
             return finish(pi, f_or(f_and(p.f[0], p.f[1]), f_and(p.f[2], p.f[3])));
         }
+    }
+
+    // The overfitting formula of trace p: its letter at every position, under
+    // nested X's, (l_0 & X (l_1 & X ( ... l_{n-1}))), l_i the conjunction of the
+    // propositions' literals at position i; when a negative extends p, also
+    // "no position after the last": l_{n-1} & !X (p0 | !p0).  It holds at
+    // position 0 of p and of no negative.  False when it does not apply (a
+    // negative equal to p; a negative extending p under NNF; a connective it
+    // needs is not allowed).
+    bool overfit(uint32_t p, const Idx &N, Fml &out) {
+        const bool has_not = (ops & LTL_NOT) != 0, nnf = (ops & LTL_NNF) != 0;
+        const uint64_t lp = offsets[p + 1] - offsets[p];
+        if (lp == 0 || (lp > 1 && !(ops & LTL_X))) return false;
+        bool need_end = false;   // some negative extends p: say that p ends
+        for (uint32_t q : N) {
+            const uint64_t lq = offsets[q + 1] - offsets[q];
+            if (lq < lp) continue;
+            bool prefix = true;
+            for (uint64_t i = 0; i < lp && prefix; ++i) prefix = letters[offsets[p] + i] == letters[offsets[q] + i];
+            if (prefix && lq == lp) return false;
+            need_end |= prefix;
+        }
+        if (need_end && (nnf || !has_not)) return false;
+        std::string f;
+        for (uint64_t i = lp; i-- > 0;) {
+            const uint32_t a = letters[offsets[p] + i];
+            std::string lam;
+            for (int b = n_props - 1; b >= 0; --b) {
+                const bool pos = (a >> b) & 1u;
+                if (!pos && !has_not) return false;
+                const std::string lit = std::string(pos ? "" : "!") + "p" + std::to_string(b);
+                lam = lam.empty() ? lit : "(" + lit + " & " + lam + ")";
+            }
+            if (i + 1 == lp) {
+                f = need_end ? "(" + lam + " & !X (p0 | !p0))" : lam;
+            } else {
+                f = "(" + lam + " & X " + f + ")";
+            }
+        }
+        out = f_text(f);
+        return true;
     }
 
     // A formula true at position 0 of every positive and false on every

@@ -191,13 +191,16 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
     L.stride = (uint64_t)L.Wt * L.plane;
     L.smem = L.G == 1 ? (size_t)(L.NB + 1) * 8 * L.stride : 0;
     L.block = L.NT;
-    // the warp-specialised kernel adds a ring of two batches of results
-    const size_t ws_smem = (size_t)(3 * L.NB + 1) * 8 * L.stride;
+    // the warp-specialised kernel adds a ring of two batches of results (its
+    // own compiled batch size)
+    const int ws_nb = L.G == 1 ? ws_kernel_batch(L.Wt, L.C, L.narrow) : 1;
+    const size_t ws_smem = (size_t)(3 * ws_nb + 1) * 8 * L.stride;
     // on request, any shape whose ring fits; the automatic choice is the
     // fused kernel (as fast on the measured workloads, less shared memory)
     const bool want_ws = level_kernel == LTL_KERNEL_WS;
     if (L.G == 1 && want_ws && ws_smem <= kWsSmemMax) {
         L.ws = true;
+        L.NB = ws_nb;
         L.smem = ws_smem;
         L.block = L.NT + kWsExtraThreads;
     }

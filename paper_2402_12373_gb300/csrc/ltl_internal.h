@@ -76,6 +76,7 @@ int fused_kernel_batch(int W, int C, bool narrow);
 const void *ws_kernel_ptr_w1(int C, int op);
 const void *ws_kernel_ptr_wn(int W, int C, int op);
 const void *ws_kernel_ptr_narrow(int C, int op);
+int ws_kernel_batch(int W, int C, bool narrow);
 constexpr int kWsExtraThreads = 64;   // the hash warps of a warp-specialised level kernel
 inline const void *fused_kernel_ptr(int W, int C, int op) {
     return W == 1 ? fused_kernel_ptr_w1(C, op) : W == 2 ? fused_kernel_ptr_w2(C, op) : fused_kernel_ptr_w48(W, C, op);

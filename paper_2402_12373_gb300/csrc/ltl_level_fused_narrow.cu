@@ -14,7 +14,10 @@ const void *fused_kernel_ptr_narrow(int C, int op) {
 
 // Candidates per batch of the fused kernel compiled for (W, C, narrow).
 int fused_kernel_batch(int W, int C, bool narrow) {
-    if (narrow) return W == 1 ? FusedNB<1, 1, true>::value : -1;   // every narrow shape: the same batch
+    if (narrow) {
+        if (W != 1) return -1;
+        return C == 1 ? FusedNB<1, 1, true>::value : C == 2 ? FusedNB<1, 2, true>::value : FusedNB<1, 4, true>::value;
+    }
     if (W * C >= 8) return FusedNB<1, 8, false>::value;
     return FusedNB<1, 1, false>::value;
 }

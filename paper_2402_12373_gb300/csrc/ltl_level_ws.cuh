@@ -23,9 +23,15 @@
 // probe round done), stored (stores and compares done), empty (slot free).
 // Every wait is bounded; a timed-out wait is made the same in every compute
 // thread (barrier reduction) before anyone acts on it, sets the problem's
-// error flag and winds the kernel down.  Probes never block on another CTA's
-// unpublished entry (DEC_WAIT is retried in a later round, after this warp
-// has published its own claims), so no two warps can wait on each other.
+// error flag and winds the kernel down.
+//
+// Progress: a probe never blocks on another CTA's unpublished entry (DEC_WAIT
+// is retried in a later round), and no claim's publication waits on another
+// CTA.  A claim of a first probe round is published once the compute threads
+// have stored its matrix, which they do right after computing the next batch
+// and before waiting for a free slot; a claim of a later round is stored and
+// published by the hash warp itself in that round.  So every entry a hash
+// warp waits for is published without depending on that warp.
 #pragma once
 #include "ltl_level_common.cuh"
 
@@ -361,6 +367,17 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
                 for (int off = 16; off > 0; off >>= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], off);
                 errs[k] = __reduce_add_sync(0xffffffffu, errs[k]);
             }
+            // first the stores and compares of the previous batch, probed while
+            // this one was computed: its hash warp then publishes its claims.
+            // This comes before waiting for a free slot, so that publishing a
+            // claim never waits on anything (a hash warp finishing a batch in
+            // its slow path may wait for another CTA's claims; those must not,
+            // in turn, wait for this CTA's slots)
+            if (pending) {
+                finish((int)((batch - 1) & 1u), (batch - 1) >> 1);
+                if (!alive) break;
+                pending = false;
+            }
             // hand the batch to the slot's hash warp
             const int slot = (int)(batch & 1u);
             if (!compute_all(lc.nt, mbar_wait_for(&sh.empty[slot], ((batch >> 1) & 1u) ^ 1u, pb.spin_limit))) {
@@ -387,11 +404,6 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
                 mt.pb = BIN ? sg.b_begin + cur_bf : 0;
             }
             mbar_arrive(&sh.full[slot]);
-            // the previous batch was probed while this one was computed
-            if (pending) {
-                finish((int)((batch - 1) & 1u), (batch - 1) >> 1);
-                if (!alive) break;
-            }
             pending = true;
             ++batch;
         }

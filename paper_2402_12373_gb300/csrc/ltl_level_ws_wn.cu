@@ -16,6 +16,12 @@ const void *ws_kernel_ptr_wn(int W, int C, int op) {
     }
 }
 
+// Candidates per batch of the warp-specialised kernel compiled for (W, C, narrow).
+int ws_kernel_batch(int W, int C, bool narrow) {
+    if (narrow) return WsNB<1, 1, true>::value;
+    return W * C >= 8 ? WsNB<1, 8, false>::value : WsNB<1, 1, false>::value;
+}
+
 const void *ws_kernel_ptr_narrow(int C, int op) {
     switch (C) {
     case 1: return ws_fn<1, 1, true>(op);
