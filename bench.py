@@ -195,6 +195,27 @@ class ClockSampler:
                 "samples": len(sm), "interval_ms": 50}
 
 
+def autotune_summary(ctx, off):
+    """The tuned launch classes: chosen configuration (tiles per resident CTA,
+    CTAs per SM below the occupancy maximum) and its best time per candidate
+    against the default configuration's (4 tiles per CTA, full occupancy)."""
+    if off:
+        return {"enabled": False}
+    tpc = [2, 4, 8, 2, 4, 8]
+    less = [0, 0, 0, 1, 1, 1]
+    chosen = {}
+    for line in ctx.autotune_dump().strip().splitlines():
+        parts = line.split()
+        conf = [tuple(map(float, p.split(":"))) for p in parts[1:]]
+        tried = [(v, c) for c, (v, n) in enumerate(conf) if n > 0]
+        if not tried:
+            continue
+        v, c = min(tried)
+        chosen[parts[0]] = {"tiles_per_cta": tpc[c], "ctas_per_sm_less": less[c], "ns_per_candidate": round(v, 3),
+                            "default_ns_per_candidate": round(conf[1][0], 3) if conf[1][1] else None}
+    return {"enabled": True, "classes": chosen}
+
+
 def cpu_baseline(target_s: float = 12.0, max_size: int = 6):
     """The oracle as it stands (single-threaded C) on the same workload,
     sizes 1..max_size enumerated completely, repeated for ~target_s."""
@@ -427,7 +448,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=8,
+                    help="untimed steps (at least 3); the launch autotuner tries its configurations in them")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed launch heuristics instead of the autotuner")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-size", type=int, default=MAX_SIZE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -479,7 +502,8 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     L.DEFAULT_LEVEL_KERNEL = {"auto": L.KERNEL_AUTO, "fused": L.KERNEL_FUSED, "ws": L.KERNEL_WS}[args.level_kernel]
-    ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks)
+    ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks,
+                    autotune=None if args.no_autotune else "")
 
     def step():
         return ctx.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
@@ -595,6 +619,7 @@ def main():
                                  "formula": found["formula"], "mode": "stop at first separator, host buffers"},
             "gpu_launches": launches,
             "clocks": clocks,
+            "autotune": autotune_summary(ctx, args.no_autotune),
         }
         if extra is not None:
             out["batched"] = bench_batched(L, ws, extra[0])

@@ -113,7 +113,17 @@ typedef struct {
     void *workspace;             /* optional caller-owned device buffer used
                                     for all device state (>= 256-byte aligned) */
     uint64_t workspace_bytes;
-    const char *autotune_path;   /* reserved, may be NULL                     */
+    const char *autotune_path;   /* online autotuning of the size-level
+                                    launches (tiles per resident CTA: 2, 4 or
+                                    8; resident CTAs per SM: the occupancy
+                                    maximum or one fewer), per kernel shape,
+                                    connective and candidate-count bucket,
+                                    from the launches' own event times.  NULL:
+                                    off (4 tiles per CTA, full occupancy);
+                                    "": tune in memory for the lifetime of the
+                                    context, batch call or server; a file
+                                    path: also read when created and written
+                                    when destroyed.  The string is copied.    */
     uint32_t max_chunks;         /* launch-shape cap: at most this many 16-byte
                                     chunks per thread (rounded up to a power of
                                     two); 0 = automatic                        */
@@ -414,6 +424,14 @@ typedef struct {
 ltl_status ltl_learn_dc(const ltl_traces *P, const ltl_traces *N, int n_props, uint32_t ops, int max_size,
                         const ltl_opts *opts, const ltl_dc_opts *dc, char *formula_out, size_t formula_cap,
                         ltl_dc_stats *stats);
+
+/* The autotuner's measurements on a context (see ltl_opts.autotune_path), as
+ * text: one line per launch class -- its key, then for each of the six
+ * configurations (tiles per CTA 2, 4, 8 at full occupancy, then the same with
+ * one CTA per SM fewer) "best ns per candidate:runs" (0:0 = untried).
+ * LTL_ERR_BUFSIZE when `cap` bytes do not hold it (*needed is set either way,
+ * terminating NUL included). */
+ltl_status ltl_ctx_autotune_dump(ltl_ctx *ctx, char *out, size_t cap, size_t *needed);
 
 /* Message of the last error on this host thread (static storage). */
 const char *ltl_last_error(void);

@@ -32,7 +32,8 @@ MAX_LEVELS = 64
 EXPORTS = ["ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_destroy", "ltl_ctx_learn",
            "ltl_ctx_learn_device", "ltl_ctx_level_range", "ltl_ctx_entry", "ltl_last_error",
            "ltl_version", "ltl_eval_noalloc", "ltl_learn_batch", "ltl_server_create", "ltl_ctx_set_mem_budget",
-           "ltl_server_submit", "ltl_server_poll", "ltl_server_pending", "ltl_server_destroy", "ltl_learn_dc"]
+           "ltl_server_submit", "ltl_server_poll", "ltl_server_pending", "ltl_server_destroy", "ltl_learn_dc",
+           "ltl_ctx_autotune_dump"]
 FORMULA_MAX = 512
 # level kernel used when a call does not choose one (tests switch it to run
 # every entry point on both kernels)
@@ -167,6 +168,8 @@ def load(build_if_missing: bool = True):
     L.ltl_learn_dc.argtypes = [TP, TP, i32, u32, i32, ctypes.POINTER(Opts), ctypes.POINTER(DcOpts), ctypes.c_char_p,
                                ctypes.c_size_t, ctypes.POINTER(DcStats)]
     L.ltl_learn_dc.restype = ctypes.c_int
+    L.ltl_ctx_autotune_dump.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.ltl_ctx_autotune_dump.restype = ctypes.c_int
     L.ltl_last_error.restype = ctypes.c_char_p
     L.ltl_version.restype = ctypes.c_char_p
     for f in ("ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_learn", "ltl_ctx_learn_device",
@@ -199,7 +202,7 @@ class _HostTraces:
 
 def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int = 0,
           spin_limit: int = 0, max_chunks: int = 0, costs=None, max_errors: int = 0, ruc: int = RUC_EXACT,
-          ruc_mask_bits: int = 0, level_kernel: Optional[int] = None) -> Opts:
+          ruc_mask_bits: int = 0, level_kernel: Optional[int] = None, autotune: Optional[str] = None) -> Opts:
     """costs: 8 connective costs (atoms, !, &, |, X, F, G, U), None = all 1;
     max_errors: misclassified traces a separator may have; ruc, ruc_mask_bits:
     cache admission policy and masked admission-key bits."""
@@ -213,7 +216,8 @@ def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int =
     o.stream = stream
     o.workspace = None
     o.workspace_bytes = 0
-    o.autotune_path = None
+    # None: fixed heuristics; "": tune in memory; a path: tune and keep the results there
+    o.autotune_path = None if autotune is None else autotune.encode()
     o.max_chunks = int(max_chunks)
     if costs is not None:
         if len(costs) != 8 or min(costs) < 1:
@@ -250,7 +254,7 @@ class Context:
     def __init__(self, workspace=None, stop: int = STOP_FIRST, stream=None, mem_budget: int = 0,
                  spin_limit: int = 0, workspace_bytes: Optional[int] = None, max_chunks: int = 0,
                  costs=None, max_errors: int = 0, ruc: int = RUC_EXACT, ruc_mask_bits: int = 0,
-                 level_kernel: Optional[int] = None):
+                 level_kernel: Optional[int] = None, autotune: Optional[str] = None):
         self._L = load()
         if workspace is None:
             workspace = default_workspace(workspace_bytes)
@@ -258,7 +262,7 @@ class Context:
         if stream is None:
             stream = _current_stream()
         self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit, max_chunks, costs, max_errors, ruc,
-                           ruc_mask_bits, level_kernel)
+                           ruc_mask_bits, level_kernel, autotune)
         h = ctypes.c_void_p()
         _check(self._L.ltl_ctx_create(ctypes.byref(self._opts), ctypes.byref(h)), ok=(LTL_OK,))
         self._h = h
@@ -279,6 +283,14 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def autotune_dump(self) -> str:
+        """The autotuner's measurements (ltl_ctx_autotune_dump)."""
+        need = ctypes.c_size_t(0)
+        self._L.ltl_ctx_autotune_dump(self._h, None, 0, ctypes.byref(need))
+        buf = ctypes.create_string_buffer(max(int(need.value), 1))
+        _check(self._L.ltl_ctx_autotune_dump(self._h, buf, len(buf), ctypes.byref(need)), ok=(LTL_OK,))
+        return buf.value.decode()
 
     def set_mem_budget(self, nbytes: int) -> None:
         _check(self._L.ltl_ctx_set_mem_budget(self._h, int(nbytes)), ok=(LTL_OK,))

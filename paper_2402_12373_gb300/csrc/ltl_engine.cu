@@ -24,6 +24,7 @@
 #include <thread>
 #include <vector>
 
+#include "ltl_autotune.h"
 #include "ltl_internal.h"
 
 namespace ltl {
@@ -240,9 +241,9 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
 }
 
 // Tile extents for a launch of `cands` candidates on `slots` resident CTAs:
-// about four tiles per CTA, never fewer than `nb` candidates per tile.
-uint32_t tile_target(uint64_t cands, uint64_t slots, int nb) {
-    uint64_t cpt = cands / std::max<uint64_t>(1, 4 * slots);
+// about `tiles_per_cta` tiles per CTA, never fewer than `nb` candidates per tile.
+uint32_t tile_target(uint64_t cands, uint64_t slots, int nb, int tiles_per_cta) {
+    uint64_t cpt = cands / std::max<uint64_t>(1, (uint64_t)tiles_per_cta * slots);
     cpt = std::max<uint64_t>(cpt, (uint64_t)nb);
     return (uint32_t)std::min<uint64_t>(pow2_ceil(cpt), (uint64_t)kTileA * kTileB);
 }
@@ -378,12 +379,18 @@ public:
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     std::vector<cudaEvent_t> ev_op;   // after each launch of a round, created on demand
     std::vector<cudaStream_t> aux;    // concurrent launches of small rounds, created on demand
+    Tuner tuner;                      // tile size and occupancy per launch class (when enabled)
     uint64_t total_rounds = 0;
 
     ~Engine() { teardown(); }
 
     ltl_status setup(const ltl_opts *o, int max_resident, bool keep) {
         opts = *o;
+        // the caller's string need not outlive this call
+        tuner.enabled = opts.autotune_path != nullptr;
+        tuner.path = opts.autotune_path ? opts.autotune_path : "";
+        opts.autotune_path = nullptr;
+        tuner.load();
         if (opts.ruc > LTL_RUC_FKP) return fail(LTL_ERR_INVALID, "ruc must be LTL_RUC_EXACT, LTL_RUC_HASH or LTL_RUC_FKP");
         if (opts.ruc_mask_bits > 62) return fail(LTL_ERR_INVALID, "ruc_mask_bits must be at most 62");
         if (opts.level_kernel > LTL_KERNEL_WS) return fail(LTL_ERR_INVALID, "level_kernel must be LTL_KERNEL_AUTO, _FUSED or _WS");
@@ -436,6 +443,7 @@ public:
     }
 
     void teardown() {
+        if (tuner.enabled) tuner.save();
         if (stream) cudaStreamSynchronize(stream);
         if (ws_owned && ws) {
             if (opts.free) opts.free(ws, stream, opts.user);
@@ -721,17 +729,33 @@ public:
         std::vector<size_t> first(groups.size());
         std::vector<uint64_t> tiles(groups.size());
         std::vector<int> grid(groups.size());
+        std::vector<uint64_t> gcands(groups.size(), 0);
         uint64_t round_cands = 0;
+        for (size_t g = 0; g < groups.size(); ++g) {
+            for (int i : groups[g].seg_ids) gcands[g] += seg_candidates(segs[i]);
+            round_cands += gcands[g];
+        }
+        const bool concurrent = groups.size() > 1 && round_cands < kConcurrentBelow;
+        std::vector<int> choice(groups.size(), -1);
+        std::vector<std::string> tkey(groups.size());
         for (size_t g = 0; g < groups.size(); ++g) {
             Group &gr = groups[g];
             int bps = 0;
             ltl_status st = occupancy(gr.fn, gr.nt, gr.smem, bps);
             if (st != LTL_OK) return st;
-            const uint64_t cap = (uint64_t)bps * (uint64_t)n_sm;
-            uint64_t cands = 0;
-            for (int i : gr.seg_ids) cands += seg_candidates(segs[i]);
-            round_cands += cands;
-            const uint32_t cpt = tile_target(cands, cap, gr.nb);
+            const uint64_t cands = gcands[g];
+            int c = kTuneDefault;
+            if (tuner.enabled && !concurrent && cands >= kTuneMinCands) {
+                const Slot &s0 = slots[segs[gr.seg_ids[0]].prob];
+                char key[96];
+                snprintf(key, sizeof key, "%s%dc%dt%d%s-op%d-b%d", s0.L.narrow ? "n" : "w", s0.L.Wt, s0.L.C, gr.nt,
+                         s0.L.ws ? "ws" : (s0.L.G > 1 ? "st" : "fu"), gr.op, ceil_log2(cands));
+                tkey[g] = key;
+                c = choice[g] = tuner.pick(tkey[g], bps > 1);
+            }
+            const TuneChoice tc = tune_choice(c);
+            const uint64_t cap = (uint64_t)std::max(1, bps - tc.cta_less) * (uint64_t)n_sm;
+            const uint32_t cpt = tile_target(cands, cap, gr.nb, tc.tiles_per_cta);
             uint64_t total = 0;
             first[g] = n_out;
             for (int i : gr.seg_ids) {
@@ -754,7 +778,6 @@ public:
         LTL_CUDA_TRY(cudaMemcpyAsync(d_segs, h_segs, sizeof(Seg) * n_out, cudaMemcpyHostToDevice, stream));
         LTL_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * groups.size(), stream));
         LTL_CUDA_TRY(cudaEventRecord(ev_begin, stream));
-        const bool concurrent = groups.size() > 1 && round_cands < kConcurrentBelow;
         if (concurrent)
             while ((int)aux.size() < kAuxStreams) {
                 cudaStream_t st = nullptr;
@@ -793,6 +816,7 @@ public:
             float t = 0.f;
             LTL_CUDA_TRY(cudaEventElapsedTime(&t, (g == 0 || concurrent) ? ev_begin : ev_op[g - 1], ev_op[g]));
             op_ms[g] = t;
+            if (choice[g] >= 0) tuner.record(tkey[g], choice[g], 1e6 * (double)t / (double)gcands[g]);
             float since = 0.f;
             LTL_CUDA_TRY(cudaEventElapsedTime(&since, ev_begin, ev_op[g]));
             round_ms = std::max(round_ms, since);
@@ -1176,6 +1200,13 @@ ltl_status ltl_learn(const ltl_traces *P, const ltl_traces *N, int n_props, uint
     s = ltl_ctx_learn(c, P, N, n_props, ops, max_size, formula_out, formula_cap, stats);
     ltl_ctx_destroy(c);
     return s;
+}
+
+ltl_status ltl_ctx_autotune_dump(ltl_ctx *c, char *out, size_t cap, size_t *needed) {
+    if (!c) return fail(LTL_ERR_INVALID, "ctx is NULL");
+    const std::string text = c->e.tuner.dump();
+    if (needed) *needed = text.size() + 1;
+    return write_formula(text, out, cap);
 }
 
 ltl_status ltl_ctx_level_range(ltl_ctx *c, int level, uint64_t *begin, uint64_t *count) {
