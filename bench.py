@@ -29,6 +29,7 @@ own independent problem (seed = rank); there is no collective on the path.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -522,6 +523,10 @@ def main():
             pass
     results = []
     times = []
+    # no cyclic-GC pass inside the timed region (the host drives every round,
+    # so a collection over the extras' inputs would stretch a step)
+    gc.collect()
+    gc.disable()
     with ClockSampler(gpu_idx) as clk:
         dist.barrier()
         torch.cuda.synchronize()
@@ -539,6 +544,7 @@ def main():
         torch.cuda.synchronize()
         clk.mark_end()
         dist.barrier()
+    gc.enable()
     clocks = clk.summary()
 
     total_ms = sum(times)
@@ -573,6 +579,8 @@ def main():
 
     # end to end: host trace buffers through ltl_ctx_learn
     e2e_times, e2e_units, h2d, d2h = [], 0, 0, 0
+    gc.collect()
+    gc.disable()
     for _ in range(max(2, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
@@ -581,6 +589,7 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
         e2e_units += units_of(r, T)
         h2d, d2h = r["h2d_bytes"], r["d2h_bytes"]
+    gc.enable()
     e2e_value = dist.reduce_sum(e2e_units, dev) / dist.reduce_max(sum(e2e_times), dev)
 
     # time to learn (stop at the first separator), host buffers, wall clock
@@ -599,6 +608,7 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "step_ms": {"median": statistics.median(times), "min": min(times), "max": max(times)},
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_traces": T, "words_per_trace": W, "max_size": K,
                        "mode": "enumeration-only (every level complete)",

@@ -144,16 +144,23 @@ typedef struct {
                                     matrices that fit one CTA                 */
 } ltl_opts;
 
-/* level_kernel values.  Both kernels compute the same candidates, counts and
+/* level_kernel values.  All kernels compute the same candidates, counts and
  * cache; they differ in how the check-and-cache step is scheduled.
- *   LTL_KERNEL_AUTO   the fused kernel (default; on the workloads measured the
- *                     two run at the same speed and the fused one needs less
- *                     shared memory)
- *   LTL_KERNEL_FUSED  all warps compute a batch, then probe and store it
+ *   LTL_KERNEL_AUTO   the fused kernel for matrices that fit one CTA (on the
+ *                     workloads measured it runs as fast as the
+ *                     warp-specialised one with less shared memory); for
+ *                     larger matrices, rounds with fewer candidates than SMs
+ *                     run the cluster kernel (a thread-block cluster holds one
+ *                     candidate in its CTAs' shared memory) when a slice
+ *                     fits, the others the two-pass streaming kernel (faster
+ *                     when every SM has candidates of its own)
+ *   LTL_KERNEL_FUSED  all warps compute a batch, then probe and store it;
+ *                     larger matrices by the two-pass streaming kernel
  *   LTL_KERNEL_WS     compute warps hand each batch to dedicated hash warps
  *                     through a shared-memory ring and compute the next one
  *                     while it is probed (when the ring fits in shared
- *                     memory; else the fused kernel) */
+ *                     memory; else the fused kernel); larger matrices by the
+ *                     cluster kernel in every round (when a slice fits) */
 enum { LTL_KERNEL_AUTO = 0, LTL_KERNEL_FUSED = 1, LTL_KERNEL_WS = 2 };
 
 #define LTL_MAX_LEVELS 64

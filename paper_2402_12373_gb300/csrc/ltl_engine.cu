@@ -45,6 +45,7 @@ constexpr int kAuxStreams = 8;
 struct Layout {
     int W = 0, Wt = 0, C = 0, NT = 0, NB = 1;
     int block = 0;          // threads per CTA: NT, plus the hash warps of the warp-specialised kernel
+    int CL = 0;             // CTAs per cluster of the cluster kernel (0: not used)
     bool narrow = false;
     bool ws = false;        // warp-specialised level kernel
     uint32_t G = 0;
@@ -142,6 +143,8 @@ struct FreeList {
 // Dynamic shared memory the warp-specialised kernel may take: what is left
 // of the opt-in maximum (227 KB) after its static part, rounded down.
 constexpr size_t kWsSmemMax = 224 * 1024;
+// Shared memory one CTA of the cluster kernel may hold its slice in.
+constexpr size_t kClusterSliceMax = 200 * 1024;
 
 ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_kernel, uint64_t budget,
                        uint64_t avail, Layout &L) {
@@ -184,6 +187,24 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
         L.C = Cmax;
         L.G = (uint32_t)((pairs + maxNT * Cmax - 1) / (maxNT * Cmax));
     }
+    // Matrices larger than one CTA: a cluster of CL CTAs (a power of two, at
+    // most 8, or 16 when 8 slices would not fit shared memory) holds one
+    // candidate in shared memory, one slice of whole chunk groups per CTA; the
+    // chunk groups are padded to a multiple of CL.  When no cluster fits, the
+    // two-pass streaming kernel runs instead.
+    if (L.G >= 2 && cluster_kernel_ptr(L.Wt, L.C) && level_kernel != LTL_KERNEL_FUSED) {
+        auto slice_bytes = [&](uint32_t cl) {
+            const uint64_t g = (L.G + cl - 1) / cl * cl;
+            return (uint64_t)L.Wt * (g / cl) * L.C * 2 * L.NT * 8;
+        };
+        uint32_t cl = 1;
+        while (cl * 2 <= 8 && cl * 2 <= L.G) cl *= 2;
+        if (slice_bytes(cl) > kClusterSliceMax && L.G >= 16) cl = 16;
+        if (slice_bytes(cl) <= kClusterSliceMax) {
+            L.CL = (int)cl;
+            L.G = (L.G + cl - 1) / cl * cl;
+        }
+    }
     // the batch size the fused kernel of this shape was compiled with (its
     // shared-memory operand slots are sized from it)
     L.NB = L.G == 1 ? fused_kernel_batch(L.Wt, L.C, L.narrow) : 1;
@@ -191,6 +212,7 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
     L.plane = (uint64_t)L.G * L.C * 2 * L.NT;   // words per bit-plane
     L.stride = (uint64_t)L.Wt * L.plane;
     L.smem = L.G == 1 ? (size_t)(L.NB + 1) * 8 * L.stride : 0;
+    if (L.CL) L.smem = (size_t)L.Wt * (L.plane / L.CL) * 8;   // the CTA's slice
     L.block = L.NT;
     // the warp-specialised kernel adds a ring of two batches of results (its
     // own compiled batch size)
@@ -365,6 +387,7 @@ public:
     };
     std::vector<Occ> occ;
     std::vector<const void *> opted_in;
+    std::vector<const void *> nonportable;   // cluster kernels allowed clusters of more than 8 CTAs
 
     int max_dynamic_smem(const void *fn) const {
         int optin = 0;
@@ -559,6 +582,30 @@ public:
         return LTL_OK;
     }
 
+    // Clusters of `cl` CTAs of a cluster kernel that can be resident at once.
+    ltl_status cluster_capacity(const void *fn, int nt, size_t smem, int cl, int &clusters) {
+        if (cl > 8 && std::find(nonportable.begin(), nonportable.end(), fn) == nonportable.end()) {
+            LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            nonportable.push_back(fn);
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)cl * (unsigned)n_sm);
+        cfg.blockDim = dim3((unsigned)nt);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        LTL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, fn, &cfg));
+        if (n < 1) return fail(LTL_ERR_INVALID, "no cluster of %d CTAs can be resident (smem %zu)", cl, smem);
+        clusters = n;
+        return LTL_OK;
+    }
+
     // Admits a problem into slot `si`: plans its layout for its budget (0: all
     // of the largest free block), takes its memory, uploads and packs its
     // traces.  Returns LTL_OK, or LTL_ERR_OOM when it does not fit right now.
@@ -656,7 +703,7 @@ public:
         s.st.batch = (uint32_t)L.NB;
         s.st.max_entries = L.max_entries;
         int bps = 0;
-        if (occupancy(kernel_for(L, OP_U), L.block, L.smem, bps) == LTL_OK) s.st.ctas_per_sm = (uint32_t)bps;
+        if (occupancy(kernel_for(L, OP_U), L.block, L.CL ? 0 : L.smem, bps) == LTL_OK) s.st.ctas_per_sm = (uint32_t)bps;
         return LTL_OK;
     }
 
@@ -708,19 +755,31 @@ public:
             int nt, op, nb;
             size_t smem;
             std::vector<int> seg_ids;
+            int cl = 0;   // cluster size of the cluster kernel
         };
         std::vector<Group> groups;
+        // Matrices larger than one CTA: the cluster kernel (one candidate over
+        // a cluster's SMs) for a problem whose round has fewer candidates than
+        // there are SMs -- the streaming kernel would leave SMs idle -- and
+        // the two-pass streaming kernel otherwise (measured faster per SM when
+        // every SM has candidates of its own).
+        std::vector<uint64_t> prob_cands(max_slots, 0);
+        for (const Seg &sg : segs) prob_cands[sg.prob] += seg_candidates(sg);
         for (int i = 0; i < (int)segs.size(); ++i) {
             const Slot &s = slots[segs[i].prob];
-            const void *fn = kernel_for(s.L, segs[i].op);
+            const bool cluster =
+                s.L.CL > 0 && (opts.level_kernel == LTL_KERNEL_WS || prob_cands[segs[i].prob] < (uint64_t)n_sm);
+            const void *fn = cluster ? cluster_kernel_ptr(s.L.Wt, s.L.C) : kernel_for(s.L, segs[i].op);
+            const int cl = cluster ? s.L.CL : 0;
+            const size_t smem = cluster ? s.L.smem : (s.L.CL ? 0 : s.L.smem);
             int g = -1;
             for (int j = 0; j < (int)groups.size(); ++j)
-                if (groups[j].fn == fn && groups[j].nt == s.L.block) g = j;
+                if (groups[j].fn == fn && groups[j].nt == s.L.block && groups[j].cl == cl) g = j;
             if (g < 0) {
-                groups.push_back(Group{fn, s.L.block, segs[i].op, s.L.NB, 0, {}});
+                groups.push_back(Group{fn, s.L.block, segs[i].op, s.L.NB, 0, {}, cl});
                 g = (int)groups.size() - 1;
             }
-            groups[g].smem = std::max(groups[g].smem, s.L.smem);
+            groups[g].smem = std::max(groups[g].smem, smem);
             groups[g].seg_ids.push_back(i);
         }
         if ((int)groups.size() > kMaxGroups) return fail(LTL_ERR_INVALID, "too many launches in one round");
@@ -751,10 +810,17 @@ public:
                 snprintf(key, sizeof key, "%s%dc%dt%d%s-op%d-b%d", s0.L.narrow ? "n" : "w", s0.L.Wt, s0.L.C, gr.nt,
                          s0.L.ws ? "ws" : (s0.L.G > 1 ? "st" : "fu"), gr.op, ceil_log2(cands));
                 tkey[g] = key;
-                c = choice[g] = tuner.pick(tkey[g], bps > 1);
+                c = choice[g] = tuner.pick(tkey[g], bps > 1 && !gr.cl);
             }
             const TuneChoice tc = tune_choice(c);
-            const uint64_t cap = (uint64_t)std::max(1, bps - tc.cta_less) * (uint64_t)n_sm;
+            // persistent workers: CTAs, or clusters for the cluster kernel
+            uint64_t cap = (uint64_t)std::max(1, bps - tc.cta_less) * (uint64_t)n_sm;
+            if (gr.cl) {
+                int nclusters = 0;
+                st = cluster_capacity(gr.fn, gr.nt, gr.smem, gr.cl, nclusters);
+                if (st != LTL_OK) return st;
+                cap = (uint64_t)nclusters;
+            }
             const uint32_t cpt = tile_target(cands, cap, gr.nb, tc.tiles_per_cta);
             uint64_t total = 0;
             first[g] = n_out;
@@ -797,8 +863,24 @@ public:
                 st = aux[g % aux.size()];
                 LTL_CUDA_TRY(cudaStreamWaitEvent(st, ev_begin, 0));
             }
-            if (grid[g] > 0)
+            if (grid[g] > 0 && groups[g].cl) {
+                // grid[g] clusters of cl CTAs
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)groups[g].cl;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3((unsigned)grid[g] * (unsigned)groups[g].cl);
+                cfg.blockDim = dim3((unsigned)groups[g].nt);
+                cfg.dynamicSmemBytes = groups[g].smem;
+                cfg.stream = st;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                LTL_CUDA_TRY(cudaLaunchKernelExC(&cfg, groups[g].fn, args));
+            } else if (grid[g] > 0) {
                 LTL_CUDA_TRY(cudaLaunchKernel(groups[g].fn, dim3(grid[g]), dim3(groups[g].nt), args, groups[g].smem, st));
+            }
             LTL_CUDA_TRY(cudaEventRecord(ev_op[g], st));
         }
         if (concurrent)
