@@ -31,8 +31,6 @@ namespace {
 
 constexpr int kClusterMax = 16;
 
-// leader states of a candidate: probe (again), or settled
-enum : int { S_DO_PROBE = 0, S_DONE_PROBE = 1 };
 
 struct ClusterShared {
     unsigned long long fp_warp[8];           // block reduction scratch
@@ -40,7 +38,7 @@ struct ClusterShared {
     int eq_warp[8];
     unsigned long long part_fp[kClusterMax];  // leader: per-CTA partials (written remotely)
     uint32_t part_err[kClusterMax];
-    uint32_t part_neq[kClusterMax];          // leader: per-CTA "slice differs" (written remotely)
+    uint32_t part_neq[kClusterMax];          // every CTA: per-CTA "slice differs" (written remotely)
     unsigned long long tile;                 // leader -> all
     int skip;
     int dec;                                 // leader -> all: DEC_NEW, DEC_CMP, or a terminal value
@@ -114,7 +112,6 @@ __device__ __forceinline__ void cluster_candidate(const Problem &pb, int level, 
     const uint64_t prov = prov_pack(OP, a, BIN ? b : 0);
     const bool leader = rank == 0 && tid == 0;
     unsigned long long key = 0, h = 0, idx = 0;
-    int state = S_DONE_PROBE;   // leader only
     if (leader) {
         uint64_t s = 0;
         uint32_t e = 0;
@@ -124,22 +121,16 @@ __device__ __forceinline__ void cluster_candidate(const Problem &pb, int level, 
         }
         if (e <= pb.max_errors) record_separator(pb, level, prov);   // eq. (dagger), or noisy
         key = admission_key(pb, s, h);
-        state = S_DO_PROBE;
     }
     for (;;) {
         if (leader) {
-            int d = DEC_DUP;   // terminal unless a probe says otherwise
-            if (state == S_DO_PROBE) {
-                d = probe<true>(pb, key, h, idx);
-                if (d != DEC_NEW && d != DEC_CMP) state = S_DONE_PROBE;
-            }
-            sh.dec = d;
+            sh.dec = probe<true>(pb, key, h, idx);
             sh.idx = idx;
         }
         cluster.sync();   // the decision is in the leader
         const int d = lead->dec;
         const unsigned long long ent_idx = lead->idx;
-        if (d != DEC_NEW && d != DEC_CMP) break;
+        if (d != DEC_NEW && d != DEC_CMP) break;   // duplicate of a settled entry, cache full, or error
         uint64_t *ent = pb.arena + ent_idx * pb.stride;
         bool eq = true;
         for (int g = 0; g < gpc; ++g) {
@@ -150,28 +141,31 @@ __device__ __forceinline__ void cluster_candidate(const Problem &pb, int level, 
             else eq &= equal_frag<W, C>(v, ent, pb.plane, toff, cs);
         }
         if (d == DEC_CMP) {
+            // this slice's verdict into every CTA of the cluster, so that all
+            // of them settle the candidate alike after the next barrier
             const int all_eq = __syncthreads_and(eq);
-            if (tid == 0) lead->part_neq[rank] = all_eq ? 0u : 1u;
+            if (tid == 0)
+                for (int q = 0; q < ncta; ++q) cluster.map_shared_rank(&sh, q)->part_neq[rank] = all_eq ? 0u : 1u;
         }
-        cluster.sync();   // every slice stored or compared
-        if (leader) {
-            if (d == DEC_NEW) {
+        cluster.sync();   // every slice stored or compared, every verdict everywhere
+        if (d == DEC_NEW) {
+            if (leader) {
                 pb.prov[ent_idx] = prov;
                 __threadfence();
                 st_release_u32(pb.hvals + h, (uint32_t)ent_idx);
-                state = S_DONE_PROBE;
-            } else {
-                uint32_t neq = 0;
-                for (int q = 0; q < ncta; ++q) neq |= sh.part_neq[q];
-                atomicAdd(&pb.ctrl->compares, 1ull);
-                if (neq) {   // same fingerprint, different matrix
-                    atomicAdd(&pb.ctrl->collisions, 1ull);
-                    h = (h + 1) & pb.hmask;
-                } else {
-                    state = S_DONE_PROBE;
-                }
+            }
+            break;
+        }
+        uint32_t neq = 0;
+        for (int q = 0; q < ncta; ++q) neq |= sh.part_neq[q];
+        if (leader) {
+            atomicAdd(&pb.ctrl->compares, 1ull);
+            if (neq) {   // same fingerprint, different matrix: probe on
+                atomicAdd(&pb.ctrl->collisions, 1ull);
+                h = (h + 1) & pb.hmask;
             }
         }
+        if (!neq) break;
     }
 }
 
