@@ -228,7 +228,10 @@ enum : int { DEC_NEW = 0, DEC_CMP = 1, DEC_FAIL = 2, DEC_ERR = 3, DEC_DUP = 4, D
 // slot's entry is not yet published, the blocking form waits (bounded); the
 // non-blocking form returns DEC_WAIT with h left on the slot, for callers that
 // may hold unpublished claims of their own (waiting there could deadlock two
-// CTAs that each wait for the other's publication).
+// CTAs that each wait for the other's publication).  Each lane takes its
+// entry index with its own atomicAdd: a warp-aggregated allocation (one
+// atomicAdd per warp after a ballot of the claims) measured slower, since the
+// warp's atomic waits for its slowest lane's CAS.
 template <bool kBlocking>
 __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, unsigned long long &h,
                                      unsigned long long &idx) {

@@ -244,8 +244,8 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
                     if (k2 < lc.lane && st2 != S_DONE && key2 == key) blocked = true;
                 }
                 int dec = DEC_DUP;
+                if (state == S_PROBE && !blocked) dec = probe<false>(pb, key, h, idx);
                 if (state == S_PROBE) {
-                    if (!blocked) dec = probe<false>(pb, key, h, idx);
                     if (blocked || dec == DEC_WAIT) {
                         // retried next round, after every CTA has published the
                         // claims of its current round (bounded by spin_limit)
@@ -292,6 +292,9 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
                 more |= (d == DEC_WAIT) || (d == DEC_CMP && ((nq >> k) & 1u));
             }
             if (lc.warp == 0) {
+                // full compares done this round, counted once for the warp
+                const uint32_t mcmp = __ballot_sync(0xffffffffu, state == S_CMP);
+                if (lc.lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
                 if (state == S_STORE) {
                     pb.prov[idx] = prov;
                     __threadfence();
@@ -305,7 +308,6 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
                     } else {
                         state = S_DONE;
                     }
-                    atomicAdd(&pb.ctrl->compares, 1ull);
                 }
                 __syncwarp();
             }
@@ -372,6 +374,9 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
     uint32_t phase = 0, round = 0;
     int cur_prob = -1;
     Problem pb;
+    // candidates of the current problem finished by this CTA, added to the
+    // problem's count when the CTA moves to another problem or ends
+    unsigned long long cands_acc = 0;
     for (;;) {
         // thread 0 takes a tile and reads its problem's stop flag
         if (lc.tid == 0) {
@@ -392,6 +397,8 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
         if (skip) continue;
         const Seg sg = la.segs[find_segment(la, tile)];
         if (sg.prob != cur_prob) {   // tiles of one problem usually come in runs
+            if (lc.tid == 0 && cands_acc) atomicAdd(&pb.ctrl->cands, cands_acc);
+            cands_acc = 0;
             cur_prob = sg.prob;
             pb = la.probs[sg.prob];
             set_lane_problem<C, NARROW>(pb, lc);
@@ -404,8 +411,9 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
         unsigned long long done = 0;
         fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done);
-        if (lc.tid == 0 && done) atomicAdd(&pb.ctrl->cands, done);
+        cands_acc += done;
     }
+    if (lc.tid == 0 && cands_acc) atomicAdd(&pb.ctrl->cands, cands_acc);
 }
 
 }  // namespace lvl

@@ -440,8 +440,8 @@ __device__ __forceinline__ int probe_round(const Problem &pb, int lane, int nb_m
         if (k2 < lane && st2 != S_DONE && key2 == key) blocked = true;
     }
     int dec = DEC_DUP;
+    if (state == S_PROBE && !blocked) dec = probe<false>(pb, key, h, idx);
     if (state == S_PROBE) {
-        if (!blocked) dec = probe<false>(pb, key, h, idx);
         if (blocked || dec == DEC_WAIT) {
             dec = DEC_WAIT;
             if (++waits > pb.spin_limit) {
@@ -464,6 +464,11 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
     uint32_t uses = 0;
     int cur_prob = -1;
     Problem pb;
+    unsigned long long cands_acc = 0;   // lane 0: candidates of the current problem, added on a change or at the end
+    auto flush = [&]() {
+        if (lane == 0 && cands_acc) atomicAdd(&pb.ctrl->cands, cands_acc);
+        cands_acc = 0;
+    };
     auto wait_all = [&](uint64_t *bar, uint32_t parity) -> bool {
         const bool ok = __all_sync(0xffffffffu, mbar_wait_for(bar, parity, spin_cap));
         if (!ok && cur_prob >= 0 && lane == 0) {
@@ -473,11 +478,18 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
         return ok;
     };
     for (;;) {
-        if (!wait_all(&sh.full[slot], uses & 1u)) return;   // the compute threads always send an end marker
+        if (!wait_all(&sh.full[slot], uses & 1u)) {   // the compute threads always send an end marker
+            flush();
+            return;
+        }
         SlotMeta<NB> &mt = sh.meta[slot];
         const int prob = mt.prob;
-        if (prob < 0) return;
+        if (prob < 0) {
+            flush();
+            return;
+        }
         if (prob != cur_prob) {
+            if (cur_prob >= 0) flush();
             cur_prob = prob;
             pb = la.probs[prob];
         }
@@ -508,8 +520,15 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
         if (lane == 0) mt.neq = 0u;
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.decided[slot]);
-        if (!wait_all(&sh.stored[slot], uses & 1u)) return;
+        if (!wait_all(&sh.stored[slot], uses & 1u)) {
+            flush();
+            return;
+        }
         const uint32_t neq0 = mt.neq;
+        {
+            const uint32_t mcmp = __ballot_sync(0xffffffffu, state == S_CMP);
+            if (lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
+        }
         if (state == S_STORE) {
             pb.prov[idx] = prov;
             __threadfence();
@@ -523,7 +542,6 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             } else {
                 state = S_DONE;
             }
-            atomicAdd(&pb.ctrl->compares, 1ull);
         }
         // rare: candidates still unsettled (another CTA's unpublished entry,
         // a key shared within the batch, a collision) are finished by this
@@ -569,6 +587,10 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                 }
             }
             __syncwarp();
+            {
+                const uint32_t mcmp = __ballot_sync(0xffffffffu, state == S_CMP);
+                if (lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
+            }
             if (state == S_STORE) {
                 pb.prov[idx] = prov;
                 __threadfence();
@@ -582,11 +604,10 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                 } else {
                     state = S_DONE;
                 }
-                atomicAdd(&pb.ctrl->compares, 1ull);
             }
             if (dec == DEC_WAIT) __nanosleep(128);
         }
-        if (lane == 0) atomicAdd(&pb.ctrl->cands, (unsigned long long)nb);
+        cands_acc += (unsigned long long)nb;
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh.empty[slot]);
         ++uses;
