@@ -124,7 +124,7 @@ __device__ __forceinline__ void cluster_candidate(const Problem &pb, int level, 
     }
     for (;;) {
         if (leader) {
-            sh.dec = probe<true>(pb, key, h, idx);
+            sh.dec = probe<true>(pb, key, h, idx, ld_volatile_i32(&pb.ctrl->cap_hit) != 0);
             sh.idx = idx;
         }
         cluster.sync();   // the decision is in the leader

@@ -234,13 +234,14 @@ enum : int { DEC_NEW = 0, DEC_CMP = 1, DEC_FAIL = 2, DEC_ERR = 3, DEC_DUP = 4, D
 // warp's atomic waits for its slowest lane's CAS.
 template <bool kBlocking>
 __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, unsigned long long &h,
-                                     unsigned long long &idx) {
+                                     unsigned long long &idx, bool full) {
+    // while the cache has room (`full`: the caller's recent reading of the
+    // cache-full flag), the CAS itself reads the slot -- one round trip for an
+    // empty slot, a match or another key; a full cache stores nothing more,
+    // so then slots are only read
     for (unsigned long long n = 0; n <= pb.hmask; ++n) {
-        unsigned long long k = ld_volatile_u64(pb.hkeys + h);
-        if (k == 0ull) {
-            // a full cache stores nothing more: an absent matrix is reported
-            // without claiming a slot, so the table keeps its load factor
-            if (ld_volatile_i32(&pb.ctrl->cap_hit)) return DEC_FAIL;
+        unsigned long long k;
+        if (!full) {
             k = atomicCAS(pb.hkeys + h, 0ull, key);
             if (k == 0ull) {
                 const unsigned long long i = atomicAdd(&pb.ctrl->n_entries, 1ull);
@@ -252,6 +253,9 @@ __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, 
                 idx = i;
                 return DEC_NEW;
             }
+        } else {
+            k = ld_volatile_u64(pb.hkeys + h);
+            if (k == 0ull) return DEC_FAIL;
         }
         if (k == key) {
             // relaxed admission: an equal key is a duplicate, whatever the matrix

@@ -70,6 +70,7 @@ struct FusedShared {
     uint32_t err[32][NB];
     unsigned long long tile;
     int skip;
+    int cap_full;   // the tile's problem had a full cache when the tile was taken
     unsigned long long idx[2][NB];
     int dec[2][NB];
     uint32_t neq[2];
@@ -86,7 +87,7 @@ template <int W, int C, int NB, int OP, bool NARROW>
 __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0, uint64_t a1,
                                            uint64_t b0, uint64_t b1, FusedShared<NB> &sh, uint64_t *slots,
                                            uint32_t &phase, uint32_t &round, const LaneConst &lc,
-                                           unsigned long long &done) {
+                                           unsigned long long &done, bool cap_full) {
     constexpr bool BIN = is_binary(OP);
     const bool tri = sg.kind == SEG_TRI;
     const uint64_t *srcA = (OP == OP_ATOM) ? pb.atoms : pb.arena;
@@ -244,7 +245,7 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
                     if (k2 < lc.lane && st2 != S_DONE && key2 == key) blocked = true;
                 }
                 int dec = DEC_DUP;
-                if (state == S_PROBE && !blocked) dec = probe<false>(pb, key, h, idx);
+                if (state == S_PROBE && !blocked) dec = probe<false>(pb, key, h, idx, cap_full);
                 if (state == S_PROBE) {
                     if (blocked || dec == DEC_WAIT) {
                         // retried next round, after every CTA has published the
@@ -381,17 +382,20 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
         // thread 0 takes a tile and reads its problem's stop flag
         if (lc.tid == 0) {
             const unsigned long long t = atomicAdd(la.tile_counter, 1ull);
-            int skip = 1;
+            int skip = 1, cap = 0;
             if (t < la.total_tiles) {
-                const int si = find_segment(la, t);
-                skip = ld_volatile_i32(&la.probs[la.segs[si].prob].ctrl->stop);
+                const Ctrl *ctrl = la.probs[la.segs[find_segment(la, t)].prob].ctrl;
+                skip = ld_volatile_i32(&ctrl->stop);
+                cap = ld_volatile_i32(&ctrl->cap_hit);
             }
             sh.tile = t;
             sh.skip = skip;
+            sh.cap_full = cap;
         }
         __syncthreads();
         const unsigned long long tile = sh.tile;
         const int skip = sh.skip;
+        const bool cap_full = sh.cap_full != 0;
         __syncthreads();
         if (tile >= la.total_tiles) break;
         if (skip) continue;
@@ -410,7 +414,7 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
         uint64_t a0, a1, b0, b1;
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
         unsigned long long done = 0;
-        fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done);
+        fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done, cap_full);
         cands_acc += done;
     }
     if (lc.tid == 0 && cands_acc) atomicAdd(&pb.ctrl->cands, cands_acc);

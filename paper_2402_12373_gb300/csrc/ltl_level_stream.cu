@@ -95,7 +95,7 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
     for (;;) {
         if (tid == 0) {
             unsigned long long h = sh.h, idx = 0;
-            sh.dec = probe<true>(pb, key, h, idx);
+            sh.dec = probe<true>(pb, key, h, idx, ld_volatile_i32(&pb.ctrl->cap_hit) != 0);
             sh.idx = idx;
             sh.h = h;
         }

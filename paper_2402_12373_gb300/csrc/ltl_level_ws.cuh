@@ -432,7 +432,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
 // a later round (DEC_WAIT).
 __device__ __forceinline__ int probe_round(const Problem &pb, int lane, int nb_max, int &state,
                                            unsigned long long key, unsigned long long &h, unsigned long long &idx,
-                                           unsigned long long &waits) {
+                                           unsigned long long &waits, bool cap_full) {
     bool blocked = false;
     for (int k2 = 0; k2 < nb_max; ++k2) {
         const unsigned long long key2 = __shfl_sync(0xffffffffu, key, k2);
@@ -440,7 +440,7 @@ __device__ __forceinline__ int probe_round(const Problem &pb, int lane, int nb_m
         if (k2 < lane && st2 != S_DONE && key2 == key) blocked = true;
     }
     int dec = DEC_DUP;
-    if (state == S_PROBE && !blocked) dec = probe<false>(pb, key, h, idx);
+    if (state == S_PROBE && !blocked) dec = probe<false>(pb, key, h, idx, cap_full);
     if (state == S_PROBE) {
         if (blocked || dec == DEC_WAIT) {
             dec = DEC_WAIT;
@@ -512,7 +512,8 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             state = S_PROBE;
         }
         // first round; the compute threads store and compare what it decided
-        probe_round(pb, lane, NB, state, key, h, idx, waits);
+        const bool cap_full = __shfl_sync(0xffffffffu, lane == 0 ? ld_volatile_i32(&pb.ctrl->cap_hit) : 0, 0) != 0;
+        probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
         if (lane < NB) {
             mt.dec[lane] = state == S_STORE ? DEC_NEW : state == S_CMP ? DEC_CMP : DEC_DUP;
             mt.idx[lane] = idx;
@@ -547,7 +548,7 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
         // a key shared within the batch, a collision) are finished by this
         // warp alone from the ring slot
         while (__any_sync(0xffffffffu, state != S_DONE)) {
-            const int dec = probe_round(pb, lane, NB, state, key, h, idx, waits);
+            const int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, ld_volatile_i32(&pb.ctrl->cap_hit) != 0);
             const uint32_t m_store = __ballot_sync(0xffffffffu, state == S_STORE);
             const uint32_t m_cmp = __ballot_sync(0xffffffffu, state == S_CMP);
             uint32_t neq = 0;
