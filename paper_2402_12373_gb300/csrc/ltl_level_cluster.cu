@@ -151,7 +151,6 @@ __device__ __forceinline__ void cluster_candidate(const Problem &pb, int level, 
         if (d == DEC_NEW) {
             if (leader) {
                 pb.prov[ent_idx] = prov;
-                __threadfence();
                 st_release_u32(pb.hvals + h, (uint32_t)ent_idx);
             }
             break;

@@ -32,6 +32,12 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     return v;
 }
 
+// Publishes an entry.  No fence is needed before it: the matrix words were
+// written before a barrier (CTA, mbarrier or cluster) that the publishing
+// thread passed, and a release at GPU scope is cumulative over writes ordered
+// before it that way; readers acquire the slot and then read the matrix
+// (PTX memory model: base causality order is transitive through each
+// release/acquire pair).
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }

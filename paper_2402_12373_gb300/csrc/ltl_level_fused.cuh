@@ -298,7 +298,6 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
                 if (lc.lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
                 if (state == S_STORE) {
                     pb.prov[idx] = prov;
-                    __threadfence();
                     st_release_u32(pb.hvals + h, (uint32_t)idx);
                     state = S_DONE;
                 } else if (state == S_CMP) {

@@ -532,7 +532,6 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
         }
         if (state == S_STORE) {
             pb.prov[idx] = prov;
-            __threadfence();
             st_release_u32(pb.hvals + h, (uint32_t)idx);
             state = S_DONE;
         } else if (state == S_CMP) {
@@ -594,7 +593,6 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             }
             if (state == S_STORE) {
                 pb.prov[idx] = prov;
-                __threadfence();
                 st_release_u32(pb.hvals + h, (uint32_t)idx);
                 state = S_DONE;
             } else if (state == S_CMP) {
