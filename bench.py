@@ -20,6 +20,8 @@ Metric: candidates x traces per second = sum over completed size levels of
            control block and formula are inside the wall-clock timed region.
   roofline the dominant kernel (the level kernel of the largest size level):
            algorithmic bytes / its event-timed duration vs measured HBM peak.
+  alu_roofline  the same launch: algorithmic 32-bit shift and logic operations
+           / its duration vs the integer throughput measured on the GPU.
   cpu_baseline  the plain C oracle, single-threaded, on a bounded sample.
 
 `--impl reference` times the oracle alone (the CPU reference of this
@@ -94,6 +96,19 @@ def op_candidates(unique, k, op, n_props):
         elif i == j:
             tot += unique[i] * (unique[i] - 1) // 2
     return tot
+
+
+def int_ops_per_candidate_trace(op, nsteps):
+    """Algorithmic 32-bit integer operations per candidate and trace in the
+    narrow layout (one 32-bit word per trace), by the operators of Section 4:
+    Not, And, Or and X one operation; F a shift and an OR per log step; G the
+    same plus the masked complement before and after; U per step a shift and a
+    three-input update of the until-vector and, on every step but the last, a
+    shift and an AND of the holds-so-far vector.  Plus 3 for the fingerprint
+    (two additions and a widening multiply-add per 64-bit word of two traces)
+    and the position-0 check."""
+    core = {1: 1, 2: 1, 3: 1, 4: 1, 5: 2 * nsteps, 6: 2 * nsteps + 2, 7: 4 * nsteps - 2}[op]
+    return core + 3
 
 
 def kernel_sources_sha():
@@ -509,6 +524,7 @@ def main():
     def step():
         return ctx.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
 
+    int_peak = L.int32_peak()   # integer roof, measured before the warm-up
     for _ in range(args.warmup):
         step()
         flush.zero_()
@@ -577,6 +593,21 @@ def main():
                 "level_ms": statistics.mean(r["ms"][kd] for r in results),
                 "kernel_sources_sha": sha}
 
+    # the same launch against the integer roof: algorithmic shift and logic
+    # operations over the measured throughput of such operations
+    alu = None
+    if r0["traces_per_word"] == 2:
+        nsteps = max(1, (spec.max_len() - 1).bit_length())
+        ops_ct = int_ops_per_candidate_trace(od, nsteps)
+        kd_ops = kd_cands * T * ops_ct
+        alu_achieved = kd_ops / (kd_ms / 1e3) / 1e9
+        alu = {"bound": "alu", "achieved": alu_achieved, "peak": int_peak["ops_per_s"] / 1e9, "unit": "Gop/s",
+               "frac": alu_achieved / (int_peak["ops_per_s"] / 1e9), "ops_per_candidate_trace": ops_ct,
+               "log_steps": nsteps, "algorithmic_ops_per_launch": kd_ops,
+               "peak_source": "measured on this GPU (ltl_int32_peak: chains of 32-bit shifts and three-input "
+                              "logic operations, %.2f ms)" % int_peak["ms"],
+               "hbm_frac_same_launch": roofline["frac"]}
+
     # end to end: host trace buffers through ltl_ctx_learn
     e2e_times, e2e_units, h2d, d2h = [], 0, 0, 0
     gc.collect()
@@ -624,6 +655,7 @@ def main():
                        "top_level_op_ms": {name: round(statistics.mean(r["op_ms"][K][op] for r in results), 4)
                                            for op, name in enumerate(OP_NAMES) if r0["op_ms"][K][op] > 0}},
             "roofline": roofline,
+            "alu_roofline": alu,
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "time_to_learn_ms": {"median": statistics.median(ttl), "size": found["size"],
                                  "formula": found["formula"], "mode": "stop at first separator, host buffers"},

@@ -440,6 +440,20 @@ ltl_status ltl_learn_dc(const ltl_traces *P, const ltl_traces *N, int n_props, u
  * terminating NUL included). */
 ltl_status ltl_ctx_autotune_dump(ltl_ctx *ctx, char *out, size_t cap, size_t *needed);
 
+/* Integer throughput of the current device, the roof for candidate launches
+ * that memory does not hold back.  The log-step loops of F, G and U (Section
+ * 4) consist of 32-bit shifts and three-input bitwise operations; this runs
+ * `iters` steps of eight independent chains of one shift and one three-input
+ * operation in every thread of 8 CTAs x 256 threads per SM, `repeats` times
+ * after one warm-up launch, on a stream of its own.
+ *   *ops_per_s  32-bit integer operations (shifts + logic operations, per
+ *               thread) per second of the fastest repeat.
+ *   *best_ms    that repeat's CUDA-event time (may be NULL).
+ * LTL_ERR_INVALID for NULL ops_per_s, iters < 4 or repeats < 1;
+ * LTL_ERR_CUDA when the device cannot run it.  Allocates 4 bytes per CTA of
+ * device memory for the duration of the call. */
+ltl_status ltl_int32_peak(int iters, int repeats, double *ops_per_s, double *best_ms);
+
 /* Message of the last error on this host thread (static storage). */
 const char *ltl_last_error(void);
 

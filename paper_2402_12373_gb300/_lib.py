@@ -33,7 +33,7 @@ EXPORTS = ["ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_destroy", "ltl_ct
            "ltl_ctx_learn_device", "ltl_ctx_level_range", "ltl_ctx_entry", "ltl_last_error",
            "ltl_version", "ltl_eval_noalloc", "ltl_learn_batch", "ltl_server_create", "ltl_ctx_set_mem_budget",
            "ltl_server_submit", "ltl_server_poll", "ltl_server_pending", "ltl_server_destroy", "ltl_learn_dc",
-           "ltl_ctx_autotune_dump"]
+           "ltl_ctx_autotune_dump", "ltl_int32_peak"]
 FORMULA_MAX = 512
 # level kernel used when a call does not choose one (tests switch it to run
 # every entry point on both kernels)
@@ -170,6 +170,8 @@ def load(build_if_missing: bool = True):
     L.ltl_learn_dc.restype = ctypes.c_int
     L.ltl_ctx_autotune_dump.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.ltl_ctx_autotune_dump.restype = ctypes.c_int
+    L.ltl_int32_peak.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.ltl_int32_peak.restype = ctypes.c_int
     L.ltl_last_error.restype = ctypes.c_char_p
     L.ltl_version.restype = ctypes.c_char_p
     for f in ("ltl_learn", "ltl_eval", "ltl_ctx_create", "ltl_ctx_learn", "ltl_ctx_learn_device",
@@ -497,3 +499,10 @@ def learn_dc(P, N, n_props: int, ops: int = ALL, max_size: int = 7, mode: int = 
 
 def version() -> str:
     return load().ltl_version().decode()
+
+
+def int32_peak(iters: int = 1 << 16, repeats: int = 3) -> Dict:
+    """Measured 32-bit shift + logic throughput of the current device (ltl_int32_peak)."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().ltl_int32_peak(iters, repeats, ctypes.byref(ops), ctypes.byref(ms)), ok=(LTL_OK,))
+    return {"ops_per_s": ops.value, "ms": ms.value}

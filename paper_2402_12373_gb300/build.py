@@ -23,7 +23,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ltl_level_fused_w1.cu", "ltl_level_fused_w2.cu", "ltl_level_fused_w48.cu",
            "ltl_level_fused_narrow.cu", "ltl_level_stream.cu", "ltl_level_cluster.cu",
            "ltl_level_ws_w1.cu", "ltl_level_ws_wn.cu",
-           "ltl_misc.cu", "ltl_host.cu", "ltl_engine.cu", "ltl_noalloc.cu", "ltl_dc.cu"]
+           "ltl_misc.cu", "ltl_host.cu", "ltl_engine.cu", "ltl_noalloc.cu", "ltl_dc.cu",
+           "ltl_peak.cu"]
 
 
 def nvcc() -> str:

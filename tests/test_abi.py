@@ -69,6 +69,11 @@ def test_host_side_validation_without_gpu():
         with pytest.raises(_lib.LtlError) as e:
             _lib.learn_dc(ts, ts, 2, **kw)
         assert e.value.status == _lib.LTL_ERR_INVALID
+    # the integer-throughput probe checks its arguments before touching a device
+    for kw in (dict(iters=3), dict(repeats=0)):
+        with pytest.raises(_lib.LtlError) as e:
+            _lib.int32_peak(**kw)
+        assert e.value.status == _lib.LTL_ERR_INVALID
 
 
 def _files(d, exts):
