@@ -474,6 +474,8 @@ def main():
                     help="skip the batched, served and trace-scaling measurements")
     ap.add_argument("--max-chunks", type=int, default=0,
                     help="launch-shape cap (16-byte chunks per thread); 0 = automatic")
+    ap.add_argument("--planning", default="auto", choices=["auto", "host"],
+                    help="where small size levels are planned (ltl_opts.level_planning)")
     ap.add_argument("--level-kernel", default="auto", choices=["auto", "fused", "ws"],
                     help="size-level kernel: automatic choice, fused, or warp-specialised")
     ap.add_argument("--ws-gb", type=float, default=0.0,
@@ -518,6 +520,7 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     L.DEFAULT_LEVEL_KERNEL = {"auto": L.KERNEL_AUTO, "fused": L.KERNEL_FUSED, "ws": L.KERNEL_WS}[args.level_kernel]
+    L.DEFAULT_PLANNING = {"auto": L.PLAN_AUTO, "host": L.PLAN_HOST}[args.planning]
     ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks,
                     autotune=None if args.no_autotune else "")
 

@@ -142,6 +142,8 @@ typedef struct {
                                     (0..62; the masking experiment, Sec. 7)   */
     uint32_t level_kernel;       /* LTL_KERNEL_*: which size-level kernel runs
                                     matrices that fit one CTA                 */
+    uint32_t level_planning;     /* LTL_PLAN_*: where the segments and tiles
+                                    of a size level are planned              */
 } ltl_opts;
 
 /* level_kernel values.  All kernels compute the same candidates, counts and
@@ -162,6 +164,18 @@ typedef struct {
  *                     memory; else the fused kernel); larger matrices by the
  *                     cluster kernel in every round (when a slice fits) */
 enum { LTL_KERNEL_AUTO = 0, LTL_KERNEL_FUSED = 1, LTL_KERNEL_WS = 2 };
+
+/* level_planning values.  A level's candidate space (Section 3) depends on how
+ * many formulas every earlier level added.
+ *   LTL_PLAN_AUTO  for one problem on the fused kernel: the levels that stay
+ *                  below 2^17 candidates even if every earlier candidate were
+ *                  new are planned on the device, one after another, and run
+ *                  back to back with one read-back for the whole chain; the
+ *                  other levels (and batches, servers, divide and conquer) are
+ *                  planned on the host after reading back the previous level
+ *   LTL_PLAN_HOST  every level planned on the host.
+ * Results, counts and formulas are the same either way. */
+enum { LTL_PLAN_AUTO = 0, LTL_PLAN_HOST = 1 };
 
 #define LTL_MAX_LEVELS 64
 

@@ -25,6 +25,7 @@ NNF = 256   # negation on atoms only (flag in the ops mask)
 RUC_EXACT, RUC_HASH, RUC_FKP = 0, 1, 2   # cache admission policies
 DC_DETERMINISTIC, DC_RANDOM = 0, 1       # divide-and-conquer split modes
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_WS = 0, 1, 2   # size-level kernel choice
+PLAN_AUTO, PLAN_HOST = 0, 1                       # where size levels are planned
 STOP_NONE, STOP_FIRST, STOP_LEVEL = 0, 1, 2
 MAX_LEVELS = 64
 
@@ -38,6 +39,8 @@ FORMULA_MAX = 512
 # level kernel used when a call does not choose one (tests switch it to run
 # every entry point on both kernels)
 DEFAULT_LEVEL_KERNEL = KERNEL_AUTO
+# level planning used when a call does not choose one
+DEFAULT_PLANNING = PLAN_AUTO
 
 
 class LtlError(RuntimeError):
@@ -61,7 +64,7 @@ class Opts(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_uint64), ("autotune_path", ctypes.c_char_p),
                 ("max_chunks", ctypes.c_uint32), ("costs", ctypes.c_uint32 * 8),
                 ("max_errors", ctypes.c_uint32), ("ruc", ctypes.c_uint32), ("ruc_mask_bits", ctypes.c_uint32),
-                ("level_kernel", ctypes.c_uint32)]
+                ("level_kernel", ctypes.c_uint32), ("level_planning", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -204,7 +207,8 @@ class _HostTraces:
 
 def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int = 0,
           spin_limit: int = 0, max_chunks: int = 0, costs=None, max_errors: int = 0, ruc: int = RUC_EXACT,
-          ruc_mask_bits: int = 0, level_kernel: Optional[int] = None, autotune: Optional[str] = None) -> Opts:
+          ruc_mask_bits: int = 0, level_kernel: Optional[int] = None, autotune: Optional[str] = None,
+          planning: Optional[int] = None) -> Opts:
     """costs: 8 connective costs (atoms, !, &, |, X, F, G, U), None = all 1;
     max_errors: misclassified traces a separator may have; ruc, ruc_mask_bits:
     cache admission policy and masked admission-key bits."""
@@ -230,6 +234,7 @@ def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int =
     o.ruc = int(ruc)
     o.ruc_mask_bits = int(ruc_mask_bits)
     o.level_kernel = int(DEFAULT_LEVEL_KERNEL if level_kernel is None else level_kernel)
+    o.level_planning = int(DEFAULT_PLANNING if planning is None else planning)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -256,7 +261,8 @@ class Context:
     def __init__(self, workspace=None, stop: int = STOP_FIRST, stream=None, mem_budget: int = 0,
                  spin_limit: int = 0, workspace_bytes: Optional[int] = None, max_chunks: int = 0,
                  costs=None, max_errors: int = 0, ruc: int = RUC_EXACT, ruc_mask_bits: int = 0,
-                 level_kernel: Optional[int] = None, autotune: Optional[str] = None):
+                 level_kernel: Optional[int] = None, autotune: Optional[str] = None,
+                 planning: Optional[int] = None):
         self._L = load()
         if workspace is None:
             workspace = default_workspace(workspace_bytes)
@@ -264,7 +270,7 @@ class Context:
         if stream is None:
             stream = _current_stream()
         self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit, max_chunks, costs, max_errors, ruc,
-                           ruc_mask_bits, level_kernel, autotune)
+                           ruc_mask_bits, level_kernel, autotune, planning)
         h = ctypes.c_void_p()
         _check(self._L.ltl_ctx_create(ctypes.byref(self._opts), ctypes.byref(h)), ok=(LTL_OK,))
         self._h = h

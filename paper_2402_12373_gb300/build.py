@@ -24,7 +24,7 @@ SOURCES = ["ltl_level_fused_w1.cu", "ltl_level_fused_w2.cu", "ltl_level_fused_w4
            "ltl_level_fused_narrow.cu", "ltl_level_stream.cu", "ltl_level_cluster.cu",
            "ltl_level_ws_w1.cu", "ltl_level_ws_wn.cu",
            "ltl_misc.cu", "ltl_host.cu", "ltl_engine.cu", "ltl_noalloc.cu", "ltl_dc.cu",
-           "ltl_peak.cu"]
+           "ltl_peak.cu", "ltl_plan.cu"]
 
 
 def nvcc() -> str:

@@ -26,6 +26,7 @@
 
 #include "ltl_autotune.h"
 #include "ltl_internal.h"
+#include "ltl_plan.h"
 
 namespace ltl {
 namespace {
@@ -262,95 +263,15 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
     return LTL_OK;
 }
 
-// Tile extents for a launch of `cands` candidates on `slots` resident CTAs:
-// about `tiles_per_cta` tiles per CTA, never fewer than `nb` candidates per tile.
-uint32_t tile_target(uint64_t cands, uint64_t slots, int nb, int tiles_per_cta) {
-    uint64_t cpt = cands / std::max<uint64_t>(1, (uint64_t)tiles_per_cta * slots);
-    cpt = std::max<uint64_t>(cpt, (uint64_t)nb);
-    return (uint32_t)std::min<uint64_t>(pow2_ceil(cpt), (uint64_t)kTileA * kTileB);
-}
-
-void set_tiles(Seg &s, uint32_t cpt) {
-    if (s.kind == SEG_UNARY) {
-        s.ta = std::min<uint32_t>(cpt, kTileU);
-        s.tb = 1;
-        s.n_tiles = (s.a_count + s.ta - 1) / s.ta;
-        return;
-    }
-    if (s.kind == SEG_TRI) {
-        uint32_t side = 2;
-        while (side < kTileA && side * side < cpt) side *= 2;
-        s.ta = s.tb = side;
-        s.n_ta = s.n_tb = (uint32_t)((s.a_count + side - 1) / side);
-        s.n_tiles = (uint64_t)s.n_ta * (s.n_ta + 1) / 2;
-        return;
-    }
-    s.tb = std::min<uint32_t>(cpt, kTileB);
-    s.ta = std::max<uint32_t>(1, std::min<uint32_t>(cpt / s.tb, kTileA));
-    s.n_ta = (uint32_t)((s.a_count + s.ta - 1) / s.ta);
-    s.n_tb = (uint32_t)((s.b_count + s.tb - 1) / s.tb);
-    s.n_tiles = (uint64_t)s.n_ta * s.n_tb;
-    s.a_inner = s.n_ta <= s.n_tb ? 1 : 0;
-}
-
-uint64_t seg_candidates(const Seg &s) {
-    if (s.kind == SEG_UNARY) return s.a_count;
-    if (s.kind == SEG_TRI) return s.a_count * (s.a_count - 1) / 2;
-    return s.a_count * s.b_count;
-}
-
-// Cost of each connective (index = op; atoms at OP_ATOM), 0 read as 1.
-struct Costs {
-    int c[8];
-};
-
-// Candidate space of cost level k of one problem (Section 3, handleOp, with the
-// cost homomorphism of Section 2; uniform cost = size), in the paper's
-// connective order F, U, G, X, And, Or, Not.
+// Candidate space of cost level k of one problem, as segments tagged with the
+// problem's slot and the level (the shared planner code of ltl_plan.h).
 void level_segments(const Slot &s, int k, int prob, const Costs &cost, std::vector<Seg> &out) {
-    auto push = [&](Seg sg) {
+    auto emit = [&](Seg sg) {
         sg.prob = prob;
         sg.level = k;
         out.push_back(sg);
     };
-    if (k == cost.c[OP_ATOM]) {
-        Seg sg{};
-        sg.op = OP_ATOM; sg.kind = SEG_UNARY; sg.a_begin = 0; sg.a_count = (uint64_t)s.in.n_props;
-        push(sg);
-        return;   // no other formula has the atoms' cost
-    }
-    const int order[7] = {OP_F, OP_U, OP_G, OP_X, OP_AND, OP_OR, OP_NOT};
-    const uint32_t bit[8] = {0, LTL_NOT, LTL_AND, LTL_OR, LTL_X, LTL_F, LTL_G, LTL_U};
-    for (int oi = 0; oi < 7; ++oi) {
-        const int op = order[oi];
-        if (!(s.in.ops & bit[op])) continue;
-        const int rest = k - cost.c[op];
-        if (op == OP_F || op == OP_G || op == OP_X || op == OP_NOT) {
-            if (rest < 1) continue;
-            if (op == OP_NOT && (s.in.ops & LTL_NNF) && rest != cost.c[OP_ATOM]) continue;   // atoms only
-            const uint64_t cnt = s.lvl_count[rest];
-            if (!cnt) continue;
-            Seg sg{};
-            sg.op = op; sg.kind = SEG_UNARY; sg.a_begin = s.lvl_begin[rest]; sg.a_count = cnt;
-            push(sg);
-            continue;
-        }
-        for (int cl = 1; cl <= rest - 1; ++cl) {
-            const int cr = rest - cl;
-            if (op != OP_U && cl > cr) continue;
-            const uint64_t na = s.lvl_count[cl], nb = s.lvl_count[cr];
-            if (!na || !nb) continue;
-            Seg sg{};
-            sg.op = op; sg.a_begin = s.lvl_begin[cl]; sg.a_count = na; sg.b_begin = s.lvl_begin[cr]; sg.b_count = nb;
-            if (op != OP_U && cl == cr) {
-                if (na < 2) continue;
-                sg.kind = SEG_TRI;
-            } else {
-                sg.kind = SEG_RECT;
-            }
-            push(sg);
-        }
-    }
+    plan_level_segments(s.in.ops, s.in.n_props, s.lvl_begin, s.lvl_count, k, cost, emit);
 }
 
 }  // namespace
@@ -370,6 +291,9 @@ public:
     bool keep_finished = false;   // contexts keep the last problem for introspection
     // shared region at the start of the workspace
     size_t o_probs = 0, o_ctrls = 0, o_segs = 0, o_counters = 0, o_jobs = 0, o_tokens = 0, o_ntok = 0, shared_end = 0;
+    size_t o_plan_state = 0, o_plan_log = 0, o_descs = 0;   // device planning of small levels
+    PlanState *h_plan_state = nullptr;
+    PlanLog *h_plan_log = nullptr;
     size_t max_segs = 0;
     Problem *h_probs = nullptr;
     Ctrl *h_ctrls = nullptr;
@@ -401,6 +325,7 @@ public:
     }
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     std::vector<cudaEvent_t> ev_op;   // after each launch of a round, created on demand
+    std::vector<cudaEvent_t> ev_chain;   // device-planned chains: per level, its start and each launch
     std::vector<cudaStream_t> aux;    // concurrent launches of small rounds, created on demand
     Tuner tuner;                      // tile size and occupancy per launch class (when enabled)
     uint64_t total_rounds = 0;
@@ -417,6 +342,7 @@ public:
         if (opts.ruc > LTL_RUC_FKP) return fail(LTL_ERR_INVALID, "ruc must be LTL_RUC_EXACT, LTL_RUC_HASH or LTL_RUC_FKP");
         if (opts.ruc_mask_bits > 62) return fail(LTL_ERR_INVALID, "ruc_mask_bits must be at most 62");
         if (opts.level_kernel > LTL_KERNEL_WS) return fail(LTL_ERR_INVALID, "level_kernel must be LTL_KERNEL_AUTO, _FUSED or _WS");
+        if (opts.level_planning > LTL_PLAN_HOST) return fail(LTL_ERR_INVALID, "level_planning must be LTL_PLAN_AUTO or _HOST");
         keep_finished = keep;
         max_slots = std::max(1, std::min(max_resident, 4096));
         cudaError_t e = cudaGetDevice(&device);
@@ -442,6 +368,9 @@ public:
         o_ctrls = take(sizeof(Ctrl) * max_slots);
         o_segs = take(sizeof(Seg) * max_segs);
         o_counters = take(sizeof(unsigned long long) * kMaxGroups);
+        o_plan_state = take(sizeof(PlanState));
+        o_plan_log = take(sizeof(PlanLog) * kMaxLevels);
+        o_descs = take(sizeof(LevelDesc) * kPlanGroups);
         o_jobs = take(sizeof(WalkJob) * max_slots);
         o_tokens = take(sizeof(uint32_t) * kMaxTokens * max_slots);
         o_ntok = take(sizeof(int) * max_slots);
@@ -452,6 +381,8 @@ public:
         LTL_CUDA_TRY(cudaMallocHost(&h_jobs, sizeof(WalkJob) * max_slots));
         LTL_CUDA_TRY(cudaMallocHost(&h_tokens, sizeof(uint32_t) * kMaxTokens * max_slots));
         LTL_CUDA_TRY(cudaMallocHost(&h_ntok, sizeof(int) * max_slots));
+        LTL_CUDA_TRY(cudaMallocHost(&h_plan_state, sizeof(PlanState)));
+        LTL_CUDA_TRY(cudaMallocHost(&h_plan_log, sizeof(PlanLog) * kMaxLevels));
         LTL_CUDA_TRY(cudaEventCreate(&ev_begin));
         LTL_CUDA_TRY(cudaEventCreate(&ev_end));
         slots.resize(max_slots);
@@ -479,13 +410,19 @@ public:
         if (h_jobs) cudaFreeHost(h_jobs);
         if (h_tokens) cudaFreeHost(h_tokens);
         if (h_ntok) cudaFreeHost(h_ntok);
+        if (h_plan_state) cudaFreeHost(h_plan_state);
+        if (h_plan_log) cudaFreeHost(h_plan_log);
         h_probs = nullptr; h_ctrls = nullptr; h_segs = nullptr; h_jobs = nullptr; h_tokens = nullptr; h_ntok = nullptr;
+        h_plan_state = nullptr; h_plan_log = nullptr;
         if (ev_begin) cudaEventDestroy(ev_begin);
         if (ev_end) cudaEventDestroy(ev_end);
         ev_begin = ev_end = nullptr;
         for (auto &ev : ev_op)
             if (ev) cudaEventDestroy(ev);
         ev_op.clear();
+        for (auto &ev : ev_chain)
+            if (ev) cudaEventDestroy(ev);
+        ev_chain.clear();
         for (auto &st : aux)
             if (st) {
                 cudaStreamSynchronize(st);
@@ -721,14 +658,231 @@ public:
         s.t_done = wall_ms();
     }
 
+    // Closes level s.level of slot si from its control block after the level:
+    // the level's counts and statistics, and whether the problem is finished
+    // (invalid input, a device error, a full cache, a separator when stopping
+    // at one, or max_size reached).
+    void close_level(int si, const Ctrl &h, std::vector<int> &found_slots) {
+        Slot &s = slots[si];
+        const int k = s.level;
+        if (h.invalid_letter) {
+            s.error = "trace letters use propositions >= n_props, offsets decrease, or a trace exceeds max_len";
+            finish(s, LTL_ERR_INVALID);
+            return;
+        }
+        if (h.err) {
+            s.error = h.err == LTL_ERR_INVALID ? "launch shape / shared memory mismatch"
+                                               : "device wait exceeded spin_limit";
+            finish(s, (ltl_status)h.err);
+            return;
+        }
+        const uint64_t ent = std::min<uint64_t>(h.n_entries, s.L.max_entries);
+        s.lvl_count[k] = ent - s.prev_entries;
+        s.st.unique[k] = ent - s.prev_entries;
+        s.st.candidates[k] = h.cands - s.prev_cands;
+        s.prev_entries = ent;
+        s.prev_cands = h.cands;
+        s.st.entries = ent;
+        const bool stopped_early = (h.stop != 0) || h.cap_hit;
+        if (!stopped_early) s.st.levels_done = k;
+        if (h.found_count > 0) s.found = true;
+        if (h.cap_hit) {
+            if (s.found) found_slots.push_back(si);
+            finish(s, s.found ? LTL_OK : LTL_CAP_REACHED);
+            return;
+        }
+        if (s.found && opts.stop_on_solution != LTL_STOP_NONE) {
+            found_slots.push_back(si);
+            finish(s, LTL_OK);
+            return;
+        }
+        if (++s.level > s.in.max_size) {
+            if (s.found) found_slots.push_back(si);
+            finish(s, s.found ? LTL_OK : LTL_NOT_FOUND);
+        }
+    }
+
+    // A level without candidates (no connective fits its cost): nothing runs.
+    void close_empty_level(int si, std::vector<int> &found_slots) {
+        Slot &s = slots[si];
+        s.lvl_count[s.level] = 0;
+        s.st.levels_done = s.level;
+        if (++s.level > s.in.max_size) {
+            if (s.found) found_slots.push_back(si);
+            finish(s, s.found ? LTL_OK : LTL_NOT_FOUND);
+        }
+    }
+
+    // Levels s.level, s.level + 1, ... that the device may plan: each stays
+    // below kConcurrentBelow candidates even if every candidate of the levels
+    // before it were new (exact for the first, whose operand counts are
+    // known; an upper bound after it).  Per level, the connectives that can
+    // have candidates (under those bounds) and their candidate bounds.
+    struct ChainLevel {
+        uint64_t cands[8];
+        bool has[8];
+    };
+    int chain_length(const Slot &s, const Costs &cost, std::vector<ChainLevel> &lv) const {
+        uint64_t beg[kMaxLevels] = {}, cnt[kMaxLevels] = {};
+        for (int j = 1; j < s.level && j < kMaxLevels; ++j) cnt[j] = s.lvl_count[j];
+        lv.clear();
+        for (int j = s.level; j <= s.in.max_size && j < kMaxLevels; ++j) {
+            ChainLevel c{};
+            uint64_t total = 0;
+            auto emit = [&](Seg sg) {
+                const uint64_t n = seg_candidates(sg);
+                c.cands[sg.op] += n;
+                c.has[sg.op] = true;
+                total += n;
+            };
+            plan_level_segments(s.in.ops, s.in.n_props, beg, cnt, j, cost, emit);
+            if (total >= kConcurrentBelow) break;
+            cnt[j] = total;
+            lv.push_back(c);
+        }
+        return (int)lv.size();
+    }
+
+    // Runs the levels of `lv` for slot si planned on the device: per level the
+    // planner kernel (closing the level before), then one launch per
+    // connective with its extent in device memory -- concurrent on the
+    // auxiliary streams -- and after the last level one more planner call
+    // that closes it.  One read-back of the level logs, then each level is
+    // closed on the host exactly as a host-planned level would be.
+    ltl_status run_chain(int si, const Costs &cost, const std::vector<ChainLevel> &lv) {
+        Slot &s = slots[si];
+        const Layout &L = s.L;
+        const int k0 = s.level, m = (int)lv.size();
+        memset(h_plan_state, 0, sizeof(PlanState));
+        for (int j = 1; j < k0; ++j) {
+            h_plan_state->lvl_begin[j] = s.lvl_begin[j];
+            h_plan_state->lvl_count[j] = s.lvl_count[j];
+        }
+        PlanState *d_state = (PlanState *)(ws + o_plan_state);
+        PlanLog *d_log = (PlanLog *)(ws + o_plan_log);
+        LevelDesc *d_desc = (LevelDesc *)(ws + o_descs);
+        Seg *d_segs = (Seg *)(ws + o_segs);
+        unsigned long long *d_counters = (unsigned long long *)(ws + o_counters);
+        LTL_CUDA_TRY(cudaMemcpyAsync(d_state, h_plan_state, sizeof(PlanState), cudaMemcpyHostToDevice, stream));
+        while ((int)aux.size() < kAuxStreams) {
+            cudaStream_t st = nullptr;
+            LTL_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            aux.push_back(st);
+        }
+        PlanArgs pa{};
+        pa.prob = (const Problem *)(ws + o_probs) + si;
+        pa.state = d_state;
+        pa.log = d_log;
+        pa.segs = d_segs;
+        pa.desc = d_desc;
+        pa.counters = d_counters;
+        pa.cost = cost;
+        pa.ops = s.in.ops;
+        pa.n_props = s.in.n_props;
+        pa.stop_mode = opts.stop_on_solution;
+        pa.prob_index = si;
+        pa.nb = L.NB;
+        pa.tiles_per_cta = tune_choice(kTuneDefault).tiles_per_cta;
+        const int per_level = 1 + kPlanGroups;   // events: level start, then one per launch
+        while ((int)ev_chain.size() < m * per_level) {
+            cudaEvent_t ev = nullptr;
+            LTL_CUDA_TRY(cudaEventCreate(&ev));
+            ev_chain.push_back(ev);
+        }
+        std::vector<std::vector<int>> level_ops(m);
+        const int order[8] = {OP_ATOM, OP_F, OP_U, OP_G, OP_X, OP_AND, OP_OR, OP_NOT};
+        for (int i = 0; i < m; ++i) {
+            const int k = k0 + i;
+            pa.n_groups = 0;
+            std::vector<const void *> fns;
+            std::vector<int> grids;
+            for (int op : order) {
+                if (!lv[i].has[op]) continue;
+                const void *fn = kernel_for(L, op);
+                int bps = 0;
+                ltl_status st = occupancy(fn, L.block, L.smem, bps);
+                if (st != LTL_OK) return st;
+                const uint64_t cap = (uint64_t)bps * (uint64_t)n_sm;
+                const uint64_t want = std::max<uint64_t>(1, (lv[i].cands[op] + L.NB - 1) / L.NB);
+                const int grid = (int)std::min<uint64_t>(cap, want);
+                pa.group_op[pa.n_groups] = op;
+                pa.group_cap[pa.n_groups] = (uint32_t)grid;
+                pa.n_groups++;
+                fns.push_back(fn);
+                grids.push_back(grid);
+                level_ops[i].push_back(op);
+            }
+            LTL_CUDA_TRY(launch_plan(pa, k, i > 0, true, stream));
+            cudaEvent_t ev_lb = ev_chain[i * per_level];
+            LTL_CUDA_TRY(cudaEventRecord(ev_lb, stream));
+            const bool concurrent = pa.n_groups > 1;
+            for (int g = 0; g < pa.n_groups; ++g) {
+                LevelArgs la{};
+                la.segs = d_segs + (size_t)g * kPlanSegsPerGroup;
+                la.probs = (const Problem *)(ws + o_probs);
+                la.tile_counter = d_counters + g;
+                la.desc = d_desc + g;
+                void *args[] = {&la};
+                cudaStream_t st = stream;
+                if (concurrent) {
+                    st = aux[g % aux.size()];
+                    LTL_CUDA_TRY(cudaStreamWaitEvent(st, ev_lb, 0));
+                }
+                LTL_CUDA_TRY(cudaLaunchKernel(fns[g], dim3(grids[g]), dim3(L.block), args, L.smem, st));
+                LTL_CUDA_TRY(cudaEventRecord(ev_chain[i * per_level + 1 + g], st));
+            }
+            if (concurrent)
+                for (int g = 0; g < pa.n_groups; ++g)
+                    LTL_CUDA_TRY(cudaStreamWaitEvent(stream, ev_chain[i * per_level + 1 + g], 0));
+        }
+        pa.n_groups = 0;
+        LTL_CUDA_TRY(launch_plan(pa, k0 + m, true, false, stream));
+        LTL_CUDA_TRY(cudaMemcpyAsync(h_plan_log + k0, d_log + k0, sizeof(PlanLog) * m, cudaMemcpyDeviceToHost, stream));
+        LTL_CUDA_TRY(cudaStreamSynchronize(stream));
+        total_rounds += (uint64_t)m;
+        std::vector<int> found_slots;
+        for (int i = 0; i < m && s.state == SLOT_RUNNING; ++i) {
+            const int k = k0 + i;
+            const PlanLog &lg = h_plan_log[k];
+            if (!lg.ran) break;   // the device stopped the chain (the host closes the same way)
+            s.st.launches += 1 + (uint32_t)level_ops[i].size();   // planner + launches
+            s.st.d2h_bytes += sizeof(PlanLog);
+            s.lvl_begin[k] = lg.begin;
+            if (lg.n_segs == 0) {
+                close_empty_level(si, found_slots);
+                continue;
+            }
+            float level_ms = 0.f;
+            for (size_t g = 0; g < level_ops[i].size(); ++g) {
+                float t = 0.f;
+                LTL_CUDA_TRY(cudaEventElapsedTime(&t, ev_chain[i * per_level], ev_chain[i * per_level + 1 + g]));
+                s.st.op_ms[k][level_ops[i][g]] = t;
+                level_ms = std::max(level_ms, t);
+            }
+            s.rounds++;
+            s.st.ms[k] = level_ms;
+            h_ctrls[si] = lg.snap;
+            close_level(si, lg.snap, found_slots);
+        }
+        s.st.launches += 1;   // the closing planner call
+        return rebuild_formulas(found_slots);
+    }
+
     // One round: the next size level of every running problem.
     ltl_status round() {
         Costs cost;
         // 0 reads as 1; anything above the largest level only bans the connective
         for (int i = 0; i < 8; ++i)
             cost.c[i] = opts.costs[i] ? (int)std::min<uint32_t>(opts.costs[i], kMaxLevels) : 1;
+        // one problem on the fused kernel: its small levels are planned on the device
+        if (opts.level_planning == LTL_PLAN_AUTO && max_slots == 1 && slots[0].state == SLOT_RUNNING &&
+            !slots[0].L.ws && slots[0].L.G == 1) {
+            std::vector<ChainLevel> lv;
+            if (chain_length(slots[0], cost, lv) >= 2) return run_chain(0, cost, lv);
+        }
         std::vector<Seg> segs;
         std::vector<int> ran;   // slots that enumerate a level this round
+        std::vector<int> found_slots;
         for (int si = 0; si < max_slots; ++si) {
             Slot &s = slots[si];
             while (s.state == SLOT_RUNNING) {
@@ -740,13 +894,10 @@ public:
                     ran.push_back(si);
                     break;
                 }
-                // no candidate of this size (no connective allowed): an empty level
-                s.lvl_count[k] = 0;
-                s.st.levels_done = k;
-                if (++s.level > s.in.max_size) finish(s, LTL_NOT_FOUND);
+                close_empty_level(si, found_slots);
             }
         }
-        if (ran.empty()) return LTL_OK;
+        if (ran.empty()) return rebuild_formulas(found_slots);
         if (segs.size() > max_segs) return fail(LTL_ERR_INVALID, "too many segments in one round");
         // group by launch (kernel, block size); a group's shared memory is the
         // largest any of its problems needs
@@ -904,7 +1055,6 @@ public:
             round_ms = std::max(round_ms, since);
         }
         // close the level of every problem that ran
-        std::vector<int> found_slots;
         for (int si : ran) {
             Slot &s = slots[si];
             const Ctrl &h = h_ctrls[si];
@@ -918,41 +1068,7 @@ public:
                         break;
                     }
             s.st.d2h_bytes += sizeof(Ctrl);
-            if (h.invalid_letter) {
-                s.error = "trace letters use propositions >= n_props, offsets decrease, or a trace exceeds max_len";
-                finish(s, LTL_ERR_INVALID);
-                continue;
-            }
-            if (h.err) {
-                s.error = h.err == LTL_ERR_INVALID ? "launch shape / shared memory mismatch"
-                                                   : "device wait exceeded spin_limit";
-                finish(s, (ltl_status)h.err);
-                continue;
-            }
-            const uint64_t ent = std::min<uint64_t>(h.n_entries, s.L.max_entries);
-            s.lvl_count[k] = ent - s.prev_entries;
-            s.st.unique[k] = ent - s.prev_entries;
-            s.st.candidates[k] = h.cands - s.prev_cands;
-            s.prev_entries = ent;
-            s.prev_cands = h.cands;
-            s.st.entries = ent;
-            const bool stopped_early = (h.stop != 0) || h.cap_hit;
-            if (!stopped_early) s.st.levels_done = k;
-            if (h.found_count > 0) s.found = true;
-            if (h.cap_hit) {
-                if (s.found) found_slots.push_back(si);
-                finish(s, s.found ? LTL_OK : LTL_CAP_REACHED);
-                continue;
-            }
-            if (s.found && opts.stop_on_solution != LTL_STOP_NONE) {
-                found_slots.push_back(si);
-                finish(s, LTL_OK);
-                continue;
-            }
-            if (++s.level > s.in.max_size) {
-                if (s.found) found_slots.push_back(si);
-                finish(s, s.found ? LTL_OK : LTL_NOT_FOUND);
-            }
+            close_level(si, h, found_slots);
         }
         // one launch per group was shared by its problems: count it once each
         for (size_t g = 0; g < groups.size(); ++g) {

@@ -90,6 +90,8 @@ cudaError_t launch_pack_narrow(const uint32_t *letters, const uint64_t *offsets,
                                cudaStream_t s);
 cudaError_t launch_keys(uint64_t *keys, uint64_t n, uint64_t seed, cudaStream_t s);
 cudaError_t launch_walk_batch(const WalkJob *jobs, int n_jobs, uint32_t *tokens, int cap, int *n_out, cudaStream_t s);
+struct PlanArgs;
+cudaError_t launch_plan(const PlanArgs &a, int k, bool close_prev, bool plan_this, cudaStream_t s);
 cudaError_t launch_eval(int W, const uint32_t *prog, int n_instr, const uint64_t *atoms, const uint64_t *mask,
                         uint64_t stride, uint64_t plane, uint64_t *stack, int nsteps, uint32_t n_traces,
                         uint64_t *out, int out_words, cudaStream_t s);

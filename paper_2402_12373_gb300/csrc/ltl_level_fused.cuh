@@ -355,6 +355,10 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     uint64_t *slots = reinterpret_cast<uint64_t *>(dyn_smem);
     __shared__ FusedShared<NB> sh;
+    if (la.desc) {   // a level planned on the device: its extent is in memory
+        la.n_segs = la.desc->n_segs;
+        la.total_tiles = la.desc->total_tiles;
+    }
     LaneConst lc;
     lc.tid = threadIdx.x;
     lc.lane = lc.tid & 31;

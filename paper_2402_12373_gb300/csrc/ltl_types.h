@@ -94,6 +94,13 @@ struct Problem {
     unsigned long long spin_limit;
 };
 
+// Extent of a launch whose level was planned on the device.
+struct LevelDesc {
+    int32_t n_segs;
+    int32_t pad;
+    uint64_t total_tiles;
+};
+
 // One launch: the segments of one connective for every problem of one launch
 // shape, each problem at its own size level.
 struct LevelArgs {
@@ -103,6 +110,7 @@ struct LevelArgs {
     int32_t n_segs;
     int32_t pad;
     uint64_t total_tiles;
+    const LevelDesc *desc;             // non-null: n_segs and total_tiles come from here
 };
 
 // One formula reconstruction: the provenance array of a problem, its entry
