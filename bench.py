@@ -267,17 +267,20 @@ def _same_result(a, b):
 
 def bench_batched(L, ws, problems):
     """Batched workload: one ltl_learn_batch call against the plain path
-    (one ltl_ctx_learn per problem, same workspace, same memory budgets)."""
+    (one ltl_ctx_learn per problem, same workspace, same memory budgets, host
+    planning of every level)."""
     import torch
     nbytes = ws.numel()
     T = [p.n_traces for p in problems]
     budgets = [int(0.85 * nbytes * t / sum(T)) for t in T]
     items = [(p.P, p.N, p.n_props, L.ALL, p.planted_size + 2, b) for p, b in zip(problems, budgets)]
-    # plain path: one problem at a time
+    # plain path: one problem at a time, every level planned on the host (for
+    # this workload of many different small problems that stop at their first
+    # separator, the faster setting of the plain path)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     alone = []
-    with L.Context(workspace=ws, stop=L.STOP_FIRST) as ctx:
+    with L.Context(workspace=ws, stop=L.STOP_FIRST, planning=L.PLAN_HOST) as ctx:
         for (P, N, n_props, ops, K, b) in items:
             ctx.set_mem_budget(b)
             alone.append(ctx.learn(P, N, n_props, ops=ops, max_size=K))

@@ -206,7 +206,12 @@ typedef struct {
                                              7 U.  Levels of fewer than 2^17
                                              candidates run their launches
                                              concurrently; there it is the time
-                                             from the level's start           */
+                                             from the level's start.  Levels
+                                             planned on the device
+                                             (LTL_PLAN_AUTO) are timed by the
+                                             device clock from one planner
+                                             call to the next; each launched
+                                             connective gets the level's time */
 } ltl_stats;
 
 /* ---------------------------------------------------------------------------

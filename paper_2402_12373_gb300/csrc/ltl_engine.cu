@@ -41,6 +41,10 @@ constexpr int kMaxGroups = 512;                       // launches per round
 // launch's time is its own.
 constexpr uint64_t kConcurrentBelow = 1ull << 17;
 constexpr int kAuxStreams = 8;
+// A chain of device-planned levels becomes a CUDA graph the eighth time its
+// shape is enqueued; up to this many shapes are kept.
+constexpr int kChainCaptureAfter = 8;
+constexpr size_t kChainShapes = 256;
 
 // Where one problem's device state lives, relative to its region base.
 struct Layout {
@@ -326,6 +330,9 @@ public:
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     std::vector<cudaEvent_t> ev_op;   // after each launch of a round, created on demand
     std::vector<cudaEvent_t> ev_chain;   // device-planned chains: per level, its start and each launch
+    std::map<std::string, cudaGraphExec_t> chain_graphs;   // captured chains by shape
+    std::map<std::string, int> chain_seen;                  // times each uncaptured shape was enqueued
+    cudaStream_t cap_stream = nullptr;   // stream chains are captured on
     std::vector<cudaStream_t> aux;    // concurrent launches of small rounds, created on demand
     Tuner tuner;                      // tile size and occupancy per launch class (when enabled)
     uint64_t total_rounds = 0;
@@ -420,6 +427,10 @@ public:
         for (auto &ev : ev_op)
             if (ev) cudaEventDestroy(ev);
         ev_op.clear();
+        for (auto &cg : chain_graphs) cudaGraphExecDestroy(cg.second);
+        chain_graphs.clear();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cap_stream = nullptr;
         for (auto &ev : ev_chain)
             if (ev) cudaEventDestroy(ev);
         ev_chain.clear();
@@ -743,6 +754,47 @@ public:
         return (int)lv.size();
     }
 
+    // The instantiated graph of a chain with this key.  Capturing and
+    // instantiating costs about as much as a few direct enqueues save, so a
+    // shape is enqueued directly (null) until it has been seen
+    // kChainCaptureAfter times; then `enqueue` is captured on a capture
+    // stream and instantiated (null when capture is not possible).
+    template <class Enqueue>
+    cudaGraphExec_t chain_graph(const std::string &key, Enqueue &enqueue) {
+        auto hit = chain_graphs.find(key);
+        if (hit != chain_graphs.end()) return hit->second;
+        if (++chain_seen[key] < kChainCaptureAfter) {
+            if (chain_seen.size() > kChainShapes) chain_seen.clear();
+            return nullptr;
+        }
+        chain_seen.erase(key);
+        if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cap_stream = nullptr;
+            return nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        const cudaError_t e = enqueue(cap_stream);
+        const cudaError_t ee = cudaStreamEndCapture(cap_stream, &g);
+        if (e != cudaSuccess || ee != cudaSuccess || !g || cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            return nullptr;
+        }
+        cudaGraphDestroy(g);
+        if (chain_graphs.size() >= kChainShapes) {
+            cudaGraphExecDestroy(chain_graphs.begin()->second);
+            chain_graphs.erase(chain_graphs.begin());
+        }
+        chain_graphs.emplace(key, exec);
+        return exec;
+    }
+
     // Runs the levels of `lv` for slot si planned on the device: per level the
     // planner kernel (closing the level before), then one launch per
     // connective with its extent in device memory -- concurrent on the
@@ -783,19 +835,32 @@ public:
         pa.prob_index = si;
         pa.nb = L.NB;
         pa.tiles_per_cta = tune_choice(kTuneDefault).tiles_per_cta;
-        const int per_level = 1 + kPlanGroups;   // events: level start, then one per launch
+        // fork / join events of the concurrent launches: level start, then one per launch
+        const int per_level = 1 + kPlanGroups;
         while ((int)ev_chain.size() < m * per_level) {
             cudaEvent_t ev = nullptr;
-            LTL_CUDA_TRY(cudaEventCreate(&ev));
+            LTL_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
             ev_chain.push_back(ev);
         }
-        std::vector<std::vector<int>> level_ops(m);
-        const int order[8] = {OP_ATOM, OP_F, OP_U, OP_G, OP_X, OP_AND, OP_OR, OP_NOT};
-        for (int i = 0; i < m; ++i) {
-            const int k = k0 + i;
-            pa.n_groups = 0;
+        // per level: the planner's arguments and the launches (connective, kernel, CTAs)
+        struct LevelLaunches {
+            PlanArgs pa;
             std::vector<const void *> fns;
             std::vector<int> grids;
+        };
+        std::vector<LevelLaunches> plan(m);
+        std::vector<std::vector<int>> level_ops(m);
+        const int order[8] = {OP_ATOM, OP_F, OP_U, OP_G, OP_X, OP_AND, OP_OR, OP_NOT};
+        std::string key((const char *)&ws, sizeof ws);   // what the enqueued work depends on
+        auto add_key = [&key](const void *p, size_t n) { key.append((const char *)p, n); };
+        add_key(&si, sizeof si);
+        add_key(&k0, sizeof k0);
+        add_key(&L.block, sizeof L.block);
+        add_key(&L.smem, sizeof L.smem);
+        for (int i = 0; i < m; ++i) {
+            LevelLaunches &ll = plan[i];
+            ll.pa = pa;
+            ll.pa.n_groups = 0;
             for (int op : order) {
                 if (!lv[i].has[op]) continue;
                 const void *fn = kernel_for(L, op);
@@ -805,39 +870,61 @@ public:
                 const uint64_t cap = (uint64_t)bps * (uint64_t)n_sm;
                 const uint64_t want = std::max<uint64_t>(1, (lv[i].cands[op] + L.NB - 1) / L.NB);
                 const int grid = (int)std::min<uint64_t>(cap, want);
-                pa.group_op[pa.n_groups] = op;
-                pa.group_cap[pa.n_groups] = (uint32_t)grid;
-                pa.n_groups++;
-                fns.push_back(fn);
-                grids.push_back(grid);
+                ll.pa.group_op[ll.pa.n_groups] = op;
+                ll.pa.group_cap[ll.pa.n_groups] = (uint32_t)grid;
+                ll.pa.n_groups++;
+                ll.fns.push_back(fn);
+                ll.grids.push_back(grid);
                 level_ops[i].push_back(op);
             }
-            LTL_CUDA_TRY(launch_plan(pa, k, i > 0, true, stream));
-            cudaEvent_t ev_lb = ev_chain[i * per_level];
-            LTL_CUDA_TRY(cudaEventRecord(ev_lb, stream));
-            const bool concurrent = pa.n_groups > 1;
-            for (int g = 0; g < pa.n_groups; ++g) {
-                LevelArgs la{};
-                la.segs = d_segs + (size_t)g * kPlanSegsPerGroup;
-                la.probs = (const Problem *)(ws + o_probs);
-                la.tile_counter = d_counters + g;
-                la.desc = d_desc + g;
-                void *args[] = {&la};
-                cudaStream_t st = stream;
-                if (concurrent) {
-                    st = aux[g % aux.size()];
-                    LTL_CUDA_TRY(cudaStreamWaitEvent(st, ev_lb, 0));
-                }
-                LTL_CUDA_TRY(cudaLaunchKernel(fns[g], dim3(grids[g]), dim3(L.block), args, L.smem, st));
-                LTL_CUDA_TRY(cudaEventRecord(ev_chain[i * per_level + 1 + g], st));
-            }
-            if (concurrent)
-                for (int g = 0; g < pa.n_groups; ++g)
-                    LTL_CUDA_TRY(cudaStreamWaitEvent(stream, ev_chain[i * per_level + 1 + g], 0));
+            add_key(&ll.pa, sizeof ll.pa);
+            add_key(ll.fns.data(), sizeof(const void *) * ll.fns.size());
+            add_key(ll.grids.data(), sizeof(int) * ll.grids.size());
         }
-        pa.n_groups = 0;
-        LTL_CUDA_TRY(launch_plan(pa, k0 + m, true, false, stream));
-        LTL_CUDA_TRY(cudaMemcpyAsync(h_plan_log + k0, d_log + k0, sizeof(PlanLog) * m, cudaMemcpyDeviceToHost, stream));
+        // the whole chain, enqueued on st0 (forking onto the auxiliary streams)
+        auto enqueue = [&](cudaStream_t st0) -> cudaError_t {
+            cudaError_t e = cudaMemcpyAsync(d_state, h_plan_state, sizeof(PlanState), cudaMemcpyHostToDevice, st0);
+            for (int i = 0; i < m && e == cudaSuccess; ++i) {
+                const LevelLaunches &ll = plan[i];
+                e = launch_plan(ll.pa, k0 + i, i > 0, true, st0);
+                cudaEvent_t ev_lb = ev_chain[i * per_level];
+                if (e == cudaSuccess) e = cudaEventRecord(ev_lb, st0);
+                const bool concurrent = ll.pa.n_groups > 1;
+                for (int g = 0; g < ll.pa.n_groups && e == cudaSuccess; ++g) {
+                    LevelArgs la{};
+                    la.segs = d_segs + (size_t)g * kPlanSegsPerGroup;
+                    la.probs = (const Problem *)(ws + o_probs);
+                    la.tile_counter = d_counters + g;
+                    la.desc = d_desc + g;
+                    void *args[] = {&la};
+                    cudaStream_t st = st0;
+                    if (concurrent) {
+                        st = aux[g % aux.size()];
+                        e = cudaStreamWaitEvent(st, ev_lb, 0);
+                    }
+                    if (e == cudaSuccess) e = cudaLaunchKernel(ll.fns[g], dim3(ll.grids[g]), dim3(L.block), args, L.smem, st);
+                    if (e == cudaSuccess) e = cudaEventRecord(ev_chain[i * per_level + 1 + g], st);
+                }
+                if (concurrent)
+                    for (int g = 0; g < ll.pa.n_groups && e == cudaSuccess; ++g)
+                        e = cudaStreamWaitEvent(st0, ev_chain[i * per_level + 1 + g], 0);
+            }
+            if (e == cudaSuccess) {
+                PlanArgs last = pa;
+                last.n_groups = 0;
+                e = launch_plan(last, k0 + m, true, false, st0);
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_plan_log + k0, d_log + k0, sizeof(PlanLog) * m, cudaMemcpyDeviceToHost, st0);
+            return e;
+        };
+        // a chain of the same shape runs as one CUDA graph, captured once
+        cudaGraphExec_t exec = chain_graph(key, enqueue);
+        if (exec) {
+            LTL_CUDA_TRY(cudaGraphLaunch(exec, stream));
+        } else {
+            LTL_CUDA_TRY(enqueue(stream));
+        }
         LTL_CUDA_TRY(cudaStreamSynchronize(stream));
         total_rounds += (uint64_t)m;
         std::vector<int> found_slots;
@@ -852,13 +939,9 @@ public:
                 close_empty_level(si, found_slots);
                 continue;
             }
-            float level_ms = 0.f;
-            for (size_t g = 0; g < level_ops[i].size(); ++g) {
-                float t = 0.f;
-                LTL_CUDA_TRY(cudaEventElapsedTime(&t, ev_chain[i * per_level], ev_chain[i * per_level + 1 + g]));
-                s.st.op_ms[k][level_ops[i][g]] = t;
-                level_ms = std::max(level_ms, t);
-            }
+            // device clock from this level's planner call to the next one
+            const float level_ms = lg.t_end > lg.t_begin ? (float)((double)(lg.t_end - lg.t_begin) * 1e-6) : 0.f;
+            for (int op : level_ops[i]) s.st.op_ms[k][op] = level_ms;
             s.rounds++;
             s.st.ms[k] = level_ms;
             h_ctrls[si] = lg.snap;

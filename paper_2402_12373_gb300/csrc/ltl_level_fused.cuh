@@ -358,6 +358,7 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
     if (la.desc) {   // a level planned on the device: its extent is in memory
         la.n_segs = la.desc->n_segs;
         la.total_tiles = la.desc->total_tiles;
+        if (la.total_tiles == 0) return;   // nothing of this connective (or the search has stopped)
     }
     LaneConst lc;
     lc.tid = threadIdx.x;

@@ -41,6 +41,8 @@ struct GroupEmit {
 // plan_this: write level k's segments, launch extents and zeroed tile counters.
 __global__ void plan_level_kernel(PlanArgs a, int k, int close_prev, int plan_this) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint64_t now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
     PlanState &st = *a.state;
     const Problem &pb = *a.prob;
     const Ctrl c = *pb.ctrl;
@@ -51,6 +53,7 @@ __global__ void plan_level_kernel(PlanArgs a, int k, int close_prev, int plan_th
         PlanLog &lg = a.log[j];
         lg.snap = c;
         lg.count = st.lvl_count[j];
+        lg.t_end = now;
         const bool found_stop = c.found_count > 0 && a.stop_mode != LTL_STOP_NONE;
         if (c.invalid_letter || c.err || c.cap_hit || found_stop) st.halted = 1;
     }
@@ -65,6 +68,8 @@ __global__ void plan_level_kernel(PlanArgs a, int k, int close_prev, int plan_th
     lg.count = 0;
     lg.n_segs = 0;
     lg.ran = 0;
+    lg.t_begin = now;
+    lg.t_end = now;
     if (st.halted) return;
     st.lvl_begin[k] = ent;
     lg.ran = 1;

@@ -145,6 +145,8 @@ struct PlanLog {
     uint64_t n_segs;   // segments planned (0: no candidate of this size)
     int32_t ran;       // 1: planned (0: the chain had halted before it)
     int32_t pad;
+    uint64_t t_begin;  // device clock (ns) when the level was planned
+    uint64_t t_end;    // device clock (ns) when it was closed
 };
 
 struct PlanArgs {

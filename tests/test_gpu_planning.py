@@ -136,6 +136,21 @@ def test_context_reuse_mixes_modes(ws):
         _same(a, b)
 
 
+@pytest.mark.parametrize("stop", [L.STOP_NONE, L.STOP_FIRST], ids=["none", "first"])
+def test_graph_replay_matches(ws, stop):
+    """A chain shape enqueued often enough runs as a captured CUDA graph; every
+    replay gives the result of host planning (the first calls are enqueued
+    directly, later ones replay the graph)."""
+    for name, P, N, n_props, K in (PROBLEMS[0], PROBLEMS[-1]):
+        host = _learn(ws, L.PLAN_HOST, stop, P, N, n_props, K, {})
+        with L.Context(workspace=ws, stop=stop, planning=L.PLAN_AUTO) as ctx:
+            for _ in range(12):
+                r = ctx.learn(P, N, n_props, max_size=K)
+                _same(r, host)
+                if r["status"] == "found":
+                    assert _errors(r["formula"], P, N, n_props) == 0, r["formula"]
+
+
 def test_invalid_planning_rejected(ws):
     with pytest.raises(L.LtlError):
         L.Context(workspace=ws, planning=2)
