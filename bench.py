@@ -104,10 +104,10 @@ def int_ops_per_candidate_trace(op, nsteps):
     Not, And, Or and X one operation; F a shift and an OR per log step; G the
     same plus the masked complement before and after; U per step a shift and a
     three-input update of the until-vector and, on every step but the last, a
-    shift and an AND of the holds-so-far vector.  Plus 3 for the fingerprint
+    shift and an AND of the holds-so-far vector; atoms none.  Plus 3 for the fingerprint
     (two additions and a widening multiply-add per 64-bit word of two traces)
     and the position-0 check."""
-    core = {1: 1, 2: 1, 3: 1, 4: 1, 5: 2 * nsteps, 6: 2 * nsteps + 2, 7: 4 * nsteps - 2}[op]
+    core = {0: 0, 1: 1, 2: 1, 3: 1, 4: 1, 5: 2 * nsteps, 6: 2 * nsteps + 2, 7: 4 * nsteps - 2}[op]
     return core + 3
 
 
