@@ -657,6 +657,7 @@ def main():
                                   "batch": r0["batch"], "ctas_per_sm": r0["ctas_per_sm"],
                                   "chunk_groups": r0["chunk_groups"]}},
             "levels": {"unique": r0["unique"][1:], "candidates": r0["candidates"][1:],
+                       "device_planned": r0["device_planned_levels"], "from_cuda_graph": r0["graph_levels"],
                        "ms": [round(x, 4) for x in r0["ms"][1:]], "entries": r0["entries"],
                        "top_level_op_ms": {name: round(statistics.mean(r["op_ms"][K][op] for r in results), 4)
                                            for op, name in enumerate(OP_NAMES) if r0["op_ms"][K][op] > 0}},

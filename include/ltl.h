@@ -212,6 +212,9 @@ typedef struct {
                                              device clock from one planner
                                              call to the next; each launched
                                              connective gets the level's time */
+    uint32_t device_planned_levels;       /* levels planned on the device       */
+    uint32_t graph_levels;                /* of those, levels run by replaying a
+                                             captured CUDA graph               */
 } ltl_stats;
 
 /* ---------------------------------------------------------------------------

@@ -78,7 +78,8 @@ class Stats(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("launches", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double),
-                ("op_ms", (ctypes.c_float * 8) * MAX_LEVELS)]
+                ("op_ms", (ctypes.c_float * 8) * MAX_LEVELS),
+                ("device_planned_levels", ctypes.c_uint32), ("graph_levels", ctypes.c_uint32)]
 
     def to_dict(self, max_size: int) -> Dict:
         K = max_size
@@ -96,6 +97,7 @@ class Stats(ctypes.Structure):
             "d2h_bytes": int(self.d2h_bytes), "max_entries": int(self.max_entries),
             "total_ms": float(self.total_ms),
             "op_ms": [[float(self.op_ms[c][o]) for o in range(8)] for c in range(K + 1)],
+            "device_planned_levels": int(self.device_planned_levels), "graph_levels": int(self.graph_levels),
         }
 
 

@@ -932,6 +932,8 @@ public:
             const int k = k0 + i;
             const PlanLog &lg = h_plan_log[k];
             if (!lg.ran) break;   // the device stopped the chain (the host closes the same way)
+            s.st.device_planned_levels++;
+            if (exec) s.st.graph_levels++;
             s.st.launches += 1 + (uint32_t)level_ops[i].size();   // planner + launches
             s.st.d2h_bytes += sizeof(PlanLog);
             s.lvl_begin[k] = lg.begin;

@@ -143,12 +143,16 @@ def test_graph_replay_matches(ws, stop):
     directly, later ones replay the graph)."""
     for name, P, N, n_props, K in (PROBLEMS[0], PROBLEMS[-1]):
         host = _learn(ws, L.PLAN_HOST, stop, P, N, n_props, K, {})
+        assert host["device_planned_levels"] == 0 and host["graph_levels"] == 0
         with L.Context(workspace=ws, stop=stop, planning=L.PLAN_AUTO) as ctx:
-            for _ in range(12):
+            for i in range(12):
                 r = ctx.learn(P, N, n_props, max_size=K)
                 _same(r, host)
                 if r["status"] == "found":
                     assert _errors(r["formula"], P, N, n_props) == 0, r["formula"]
+                assert r["device_planned_levels"] >= 1
+                # direct enqueues first; from the eighth call of the shape on, a graph
+                assert (r["graph_levels"] == r["device_planned_levels"]) == (i >= 7), (i, r["graph_levels"])
 
 
 def test_invalid_planning_rejected(ws):
