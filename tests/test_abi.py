@@ -69,6 +69,19 @@ def test_host_side_validation_without_gpu():
         with pytest.raises(_lib.LtlError) as e:
             _lib.learn_dc(ts, ts, 2, **kw)
         assert e.value.status == _lib.LTL_ERR_INVALID
+    # option values are checked before any CUDA call
+    import ctypes
+    lib = _lib.load()
+    hp = _lib._HostTraces(ts)
+    for field, bad in (("level_planning", 2), ("level_kernel", 3), ("ruc", 3), ("ruc_mask_bits", 63)):
+        o = _lib._opts()
+        setattr(o, field, bad)
+        buf = ctypes.create_string_buffer(64)
+        st = _lib.Stats()
+        rc = lib.ltl_learn(ctypes.byref(hp.struct), ctypes.byref(hp.struct), 2, _lib.ALL, 3, ctypes.byref(o), buf,
+                           len(buf), ctypes.byref(st))
+        assert rc == _lib.LTL_ERR_INVALID, field
+        assert field.split("_")[0] in _lib.last_error(), (field, _lib.last_error())
     # the integer-throughput probe checks its arguments before touching a device
     for kw in (dict(iters=3), dict(repeats=0)):
         with pytest.raises(_lib.LtlError) as e:
