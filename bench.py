@@ -5,7 +5,8 @@ Workload (the single-large learning problem): 3 propositions, 1024 positive +
 1024 negative seeded synthetic traces of length U{16..32}, Bernoulli(0.3)
 proposition bits, labelled by the planted formula (G(!p0 | F p1) | p2); all
 seven connectives; sizes 1..9, every level enumerated completely
-(enumeration-only mode), the language cache and hash set resident in HBM.
+(enumeration-only mode), the language cache and hash set resident in HBM
+within a 32 GB memory budget.
 
 One step = one whole learn call (trace packing, then every size level's
 candidate kernel, reading back the control block after each level).
@@ -481,6 +482,9 @@ def main():
                     help="where small size levels are planned (ltl_opts.level_planning)")
     ap.add_argument("--level-kernel", default="auto", choices=["auto", "fused", "ws"],
                     help="size-level kernel: automatic choice, fused, or warp-specialised")
+    ap.add_argument("--budget-gb", type=float, default=32.0,
+                    help="device memory budget of the single-large problem's cache and hash set, in GB "
+                         "(capped by the workspace)")
     ap.add_argument("--ws-gb", type=float, default=0.0,
                     help="workspace size in GB (default: half of the free device memory)")
     args = ap.parse_args()
@@ -524,7 +528,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     L.DEFAULT_LEVEL_KERNEL = {"auto": L.KERNEL_AUTO, "fused": L.KERNEL_FUSED, "ws": L.KERNEL_WS}[args.level_kernel]
     L.DEFAULT_PLANNING = {"auto": L.PLAN_AUTO, "host": L.PLAN_HOST}[args.planning]
-    ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks,
+    budget = int(args.budget_gb * 1e9)
+    ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks, mem_budget=budget,
                     autotune=None if args.no_autotune else "")
 
     def step():
@@ -630,7 +635,7 @@ def main():
     e2e_value = dist.reduce_sum(e2e_units, dev) / dist.reduce_max(sum(e2e_times), dev)
 
     # time to learn (stop at the first separator), host buffers, wall clock
-    ctx_first = L.Context(workspace=ws, stop=L.STOP_FIRST)
+    ctx_first = L.Context(workspace=ws, stop=L.STOP_FIRST, mem_budget=budget)
     ttl = []
     found = None
     for _ in range(5):
@@ -650,6 +655,7 @@ def main():
             "config": {"workload": WORKLOAD, "n_traces": T, "words_per_trace": W, "max_size": K,
                        "mode": "enumeration-only (every level complete)",
                        "l2": "flushed between steps (512 MiB write); cache working set > L2",
+                       "memory_budget_gb": min(args.budget_gb, ws_bytes / 1e9),
                        "parallelism": "independent problem per rank (seed = rank)" if world > 1 else "1 GPU",
                        "launch": {"threads_per_cta": r0["threads_per_cta"],
                                   "traces_per_thread": r0["traces_per_thread"],
