@@ -139,7 +139,13 @@ typedef struct {
                                     (default), LTL_RUC_HASH or LTL_RUC_FKP    */
     uint32_t ruc_mask_bits;      /* relaxed modes: zero this many of the 63
                                     admission-key bits, the highest first
-                                    (0..62; the masking experiment, Sec. 7)   */
+                                    (0..62; the masking experiment, Sec. 7).
+                                    LTL_RUC_EXACT: the same bits of the
+                                    fingerprint key are zeroed, so that more
+                                    candidates meet an equal key of a
+                                    different matrix; the full compare still
+                                    decides, results stay exact (a stress
+                                    setting for the collision path)          */
     uint32_t level_kernel;       /* LTL_KERNEL_*: which size-level kernel runs
                                     matrices that fit one CTA                 */
     uint32_t level_planning;     /* LTL_PLAN_*: where the segments and tiles
@@ -215,6 +221,10 @@ typedef struct {
     uint32_t device_planned_levels;       /* levels planned on the device       */
     uint32_t graph_levels;                /* of those, levels run by replaying a
                                              captured CUDA graph               */
+    uint64_t compares;                    /* full-matrix compares after an
+                                             equal key (exact admission)       */
+    uint64_t collisions;                  /* compares that found a different
+                                             matrix (probing went on)          */
 } ltl_stats;
 
 /* ---------------------------------------------------------------------------

@@ -79,7 +79,8 @@ class Stats(ctypes.Structure):
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double),
                 ("op_ms", (ctypes.c_float * 8) * MAX_LEVELS),
-                ("device_planned_levels", ctypes.c_uint32), ("graph_levels", ctypes.c_uint32)]
+                ("device_planned_levels", ctypes.c_uint32), ("graph_levels", ctypes.c_uint32),
+                ("compares", ctypes.c_uint64), ("collisions", ctypes.c_uint64)]
 
     def to_dict(self, max_size: int) -> Dict:
         K = max_size
@@ -98,6 +99,7 @@ class Stats(ctypes.Structure):
             "total_ms": float(self.total_ms),
             "op_ms": [[float(self.op_ms[c][o]) for o in range(8)] for c in range(K + 1)],
             "device_planned_levels": int(self.device_planned_levels), "graph_levels": int(self.graph_levels),
+            "compares": int(self.compares), "collisions": int(self.collisions),
         }
 
 

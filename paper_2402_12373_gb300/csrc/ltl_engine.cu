@@ -695,6 +695,8 @@ public:
         s.prev_entries = ent;
         s.prev_cands = h.cands;
         s.st.entries = ent;
+        s.st.compares = h.compares;
+        s.st.collisions = h.collisions;
         const bool stopped_early = (h.stop != 0) || h.cap_hit;
         if (!stopped_early) s.st.levels_done = k;
         if (h.found_count > 0) s.found = true;

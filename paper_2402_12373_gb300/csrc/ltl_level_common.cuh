@@ -309,7 +309,10 @@ __device__ __forceinline__ unsigned long long fp_key(uint64_t s) {
 // equality of the 63-bit values; the slot comes from a finalised copy.
 __device__ __forceinline__ unsigned long long admission_key(const Problem &pb, uint64_t s, unsigned long long &h) {
     if (pb.ruc == RUC_EXACT) {
-        const unsigned long long key = fp_key(s);
+        unsigned long long key = fp_key(s);
+        // masked fingerprints (a stress setting): more equal keys of different
+        // matrices, still told apart by the full compare
+        if (pb.key_mask != kKey63) key = (key & pb.key_mask) | (1ull << 63);
         h = key & pb.hmask;
         return key;
     }
