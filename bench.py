@@ -528,7 +528,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     L.DEFAULT_LEVEL_KERNEL = {"auto": L.KERNEL_AUTO, "fused": L.KERNEL_FUSED, "ws": L.KERNEL_WS}[args.level_kernel]
     L.DEFAULT_PLANNING = {"auto": L.PLAN_AUTO, "host": L.PLAN_HOST}[args.planning]
-    budget = int(args.budget_gb * 1e9)
+    budget = min(int(args.budget_gb * 1e9), int(ws_bytes * 0.9))   # the workspace also holds the fixed parts
     ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks, mem_budget=budget,
                     autotune=None if args.no_autotune else "")
 
@@ -655,7 +655,7 @@ def main():
             "config": {"workload": WORKLOAD, "n_traces": T, "words_per_trace": W, "max_size": K,
                        "mode": "enumeration-only (every level complete)",
                        "l2": "flushed between steps (512 MiB write); cache working set > L2",
-                       "memory_budget_gb": min(args.budget_gb, ws_bytes / 1e9),
+                       "memory_budget_gb": budget / 1e9,
                        "parallelism": "independent problem per rank (seed = rank)" if world > 1 else "1 GPU",
                        "launch": {"threads_per_cta": r0["threads_per_cta"],
                                   "traces_per_thread": r0["traces_per_thread"],
