@@ -95,7 +95,11 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
     for (;;) {
         if (tid == 0) {
             unsigned long long h = sh.h, idx = 0;
-            sh.dec = probe<true>(pb, key, h, idx, ld_volatile_i32(&pb.ctrl->cap_hit) != 0);
+            // Once the cache is full nothing more is stored: the candidate has
+            // been checked for separation above, and whether it duplicates an
+            // entry no longer matters, so neither the probe nor the second
+            // pass (the compare) is run.
+            sh.dec = ld_volatile_i32(&pb.ctrl->cap_hit) ? (int)DEC_FAIL : probe<true>(pb, key, h, idx, false);
             sh.idx = idx;
             sh.h = h;
         }
