@@ -818,7 +818,6 @@ public:
         LevelDesc *d_desc = (LevelDesc *)(ws + o_descs);
         Seg *d_segs = (Seg *)(ws + o_segs);
         unsigned long long *d_counters = (unsigned long long *)(ws + o_counters);
-        LTL_CUDA_TRY(cudaMemcpyAsync(d_state, h_plan_state, sizeof(PlanState), cudaMemcpyHostToDevice, stream));
         while ((int)aux.size() < kAuxStreams) {
             cudaStream_t st = nullptr;
             LTL_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
