@@ -603,6 +603,9 @@ def main():
                 "candidates_per_launch": kd_cands, "launch_ms": kd_ms,
                 "level_ms": statistics.mean(r["ms"][kd] for r in results),
                 "kernel_sources_sha": sha}
+    if roofline["traffic"]:
+        # physical DRAM bandwidth of the launch: profiled bytes over its event time
+        roofline["dram_gbs"] = roofline["traffic"] / (kd_ms / 1e3) / 1e9
 
     # the same launch against the integer roof: algorithmic shift and logic
     # operations over the measured throughput of such operations
