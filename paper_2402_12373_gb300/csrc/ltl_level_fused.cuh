@@ -83,8 +83,9 @@ struct LaneConst {
     int tid, lane, warp, nwarps;
 };
 
+// Returns false when an operand wait ran out (the CTA must take no more tiles).
 template <int W, int C, int NB, int OP, bool NARROW>
-__device__ __forceinline__ void fused_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0, uint64_t a1,
+__device__ __forceinline__ bool fused_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0, uint64_t a1,
                                            uint64_t b0, uint64_t b1, FusedShared<NB> &sh, uint64_t *slots,
                                            uint32_t &phase, uint32_t &round, const LaneConst &lc,
                                            unsigned long long &done, bool cap_full) {
@@ -137,16 +138,14 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
         }
         if (BIN) loaded_a = a;
     };
-    auto wait_data = [&]() {
+    // false when the wait ran out: this thread has not seen the batch land,
+    // and keeps the phase so that the copies can still be waited for
+    auto wait_data = [&]() -> bool {
         unsigned long long spins = 0;
-        while (!mbar_try_wait(&sh.bar, phase)) {
-            if (++spins > pb.spin_limit) {
-                atomicCAS(&pb.ctrl->err, 0, -4 /* LTL_ERR_TIMEOUT */);
-                atomicExch(&pb.ctrl->stop, 1);
-                break;
-            }
-        }
+        while (!mbar_try_wait(&sh.bar, phase))
+            if (++spins > pb.spin_limit) return false;
         phase ^= 1u;
+        return true;
     };
 
     uint64_t a, bf;
@@ -154,22 +153,34 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
     bool have = next(a, bf, nb);
     if (have) issue(a, bf, nb);
     while (have) {
-        wait_data();
+        const bool landed = wait_data();
         // ---- 2. candidates of the batch in registers
         constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
         Frag<W, C> r[NB];
         uint64_t fp[NB];
         uint32_t errs[NB];
+        if constexpr (OP == OP_U) {
+            // the batch shares its left operand (slot NB); slots k >= nb hold
+            // an earlier batch's operands, computed and then ignored
+            Frag<W, C> x;
+            load_frag<W, C, false>(slots + (uint64_t)NB * lc.stride, lc.plane, lc.toff, lc.cs, x);
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                load_frag<W, C, false>(slots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
+            apply_binary_batch<OP, W, C, NB, NARROW>(r, x, pb.nsteps);
+        }
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             fp[k] = 0;
             errs[k] = 0;
             if (k < nb) {
-                Frag<W, C> x, m;
-                load_frag<W, C, false>(slots + (uint64_t)(BIN ? NB : k) * lc.stride, lc.plane, lc.toff, lc.cs, x);
-                if (BIN) load_frag<W, C, false>(slots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
-                if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
-                apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps);
+                if constexpr (OP != OP_U) {
+                    Frag<W, C> x, m;
+                    load_frag<W, C, false>(slots + (uint64_t)(BIN ? NB : k) * lc.stride, lc.plane, lc.toff, lc.cs, x);
+                    if (BIN) load_frag<W, C, false>(slots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
+                    if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
+                    apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps);
+                }
                 const uint32_t bits = pos0_bits<W, C, NARROW>(r[k]);
                 errs[k] = (uint32_t)__popc((bits ^ lc.want) & lc.care);   // misclassified traces
             }
@@ -209,7 +220,24 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
                 sh.err[lc.warp][k] = errs[k];
             }
         }
-        __syncthreads();
+        // the reduction's barrier also makes the wait's outcome uniform: if
+        // any thread gave up, the batch's matrices may have been computed from
+        // shared memory the copies had not filled yet, so nothing of it is
+        // checked or admitted, no further copy is issued, and the CTA waits
+        // (again bounded) for the copies still in flight before it stops
+        if (__syncthreads_or(landed ? 0 : 1)) {
+            if (lc.tid == 0) {
+                atomicCAS(&pb.ctrl->err, 0, -4 /* LTL_ERR_TIMEOUT */);
+                atomicExch(&pb.ctrl->stop, 1);
+            }
+            if (!landed) {
+                unsigned long long spins = 0;
+                while (!mbar_try_wait(&sh.bar, phase) && ++spins < (1ull << 26)) {
+                }
+            }
+            __syncthreads();
+            return false;
+        }
         const uint64_t cur_a = a, cur_bf = bf;
         const int cur_nb = nb;
         have = next(a, bf, nb);
@@ -316,6 +344,7 @@ __device__ __forceinline__ void fused_tile(const Problem &pb, int level, const S
         }
         done += (unsigned long long)cur_nb;
     }
+    return true;
 }
 
 }  // namespace
@@ -418,8 +447,10 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
         uint64_t a0, a1, b0, b1;
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
         unsigned long long done = 0;
-        fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done, cap_full);
+        const bool ok =
+            fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done, cap_full);
         cands_acc += done;
+        if (!ok) break;
     }
     if (lc.tid == 0 && cands_acc) atomicAdd(&pb.ctrl->cands, cands_acc);
 }
