@@ -162,6 +162,50 @@ __device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Fra
     }
 }
 
+// A binary connective on a batch of NB candidates that share the left operand
+// a (r[k] = right operand k on entry, the result on exit).  For U the left
+// operand's own propagation (Lemma 2: "f holds on [j, j + 2^i)") does not
+// depend on the right operand, so it runs once per batch, and each step costs
+// every candidate one shift and one three-input logic operation.  Slots
+// k >= nb hold zeros and are computed like the others (uniform control flow).
+template <int OP, int W, int C, int NB, bool NARROW = false>
+__device__ __forceinline__ void apply_binary_batch(Frag<W, C> (&r)[NB], Frag<W, C> &a, int nsteps) {
+    if (OP == OP_AND || OP == OP_OR) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int w = 0; w < W; ++w)
+                        r[k].v[c][j][w] =
+                            (OP == OP_AND) ? (r[k].v[c][j][w] & a.v[c][j][w]) : (r[k].v[c][j][w] | a.v[c][j][w]);
+    } else if (OP == OP_U) {
+        for (int i = 0; i < nsteps; ++i) {
+            const uint32_t s = 1u << i;
+            const bool last = (i + 1 == nsteps);
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    uint64_t t[W];
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        shr_any<W, NARROW>(r[k].v[c][j], s, t);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) r[k].v[c][j][w] |= a.v[c][j][w] & t[w];
+                    }
+                    if (!last) {
+                        shr_any<W, NARROW>(a.v[c][j], s, t);
+#pragma unroll
+                        for (int w = 0; w < W; ++w) a.v[c][j][w] &= t[w];
+                    }
+                }
+        }
+    }
+}
+
 // Soundness bits of this thread's traces: the value at position 0 of trace
 // slot (c, j) is bit 2c + j; in the narrow layout word (c, j) holds two
 // traces, at bits 4c + 2j (even trace) and 4c + 2j + 1 (odd trace).
