@@ -375,7 +375,10 @@ void ltl_server_destroy(ltl_server *srv);
  *   d_letters,       the traces, already in DEVICE memory (layout as in
  *   d_offsets        ltl_traces); read only.
  *   n_traces         number of traces.
- *   max_len          >= the longest trace (<= 1024).
+ *   max_len          >= the longest trace (<= 1024).  A trace longer than
+ *                    max_len but within 64 * ceil(max_len / 64) positions is
+ *                    still evaluated exactly; a longer one is rejected with
+ *                    LTL_ERR_INVALID.
  *   d_cs_out         DEVICE buffer of n_traces * words_per_trace uint64, trace
  *                    major as for ltl_eval, written by the call.
  *   words_per_trace  >= ceil(max_len / 64).
@@ -390,8 +393,9 @@ void ltl_server_destroy(ltl_server *srv);
  * contents; each call clears what must start at zero.  Calls whose work
  * overlaps on the GPU (other streams or host threads) race on the array: the
  * caller must serialise them.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.
+ * array's device address (cudaGetSymbolAddress, with that device current).
+ * Every call also reads a status word back to the host and synchronises the
+ * stream, so no call may be made while a stream is being captured.
  * -------------------------------------------------------------------------*/
 #define LTL_NOALLOC_SCRATCH_BYTES (64ull << 20)
 ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_letters, const uint64_t *d_offsets,

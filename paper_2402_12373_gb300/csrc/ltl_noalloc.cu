@@ -18,8 +18,9 @@
 //    streams, or different host threads) race on it and must be serialised by
 //    the caller;
 //  * its device address is looked up once per device, by the first call on
-//    that device (cudaGetSymbolAddress, with that device current); make that
-//    first call before any stream capture.
+//    that device (cudaGetSymbolAddress, with that device current);
+//  * every call reads a status word back into host memory and synchronises
+//    the stream, so no call can be made while a stream is being captured.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -124,8 +125,12 @@ extern "C" ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_le
     NOALLOC_TRY(cudaMemsetAsync(mask, 0, (size_t)(o_stack - o_mask), sm));
     NOALLOC_TRY(cudaMemcpyAsync(scr + o_prog, prog.data(), 4 * prog.size(), cudaMemcpyHostToDevice, sm));
     NOALLOC_TRY(launch_pack(d_letters, d_offsets, (uint32_t)n_traces, plane, W, n_props, mask, atoms, stride, ctrl, sm));
+    // log steps for the packed capacity (64 * W positions), not for max_len:
+    // the pack kernel accepts any trace that fits W words, and a trace longer
+    // than max_len evaluated with max_len's steps would lose the F / G / U
+    // bits beyond 2^steps (extra steps are harmless)
     int nsteps = 0;
-    while ((1ull << nsteps) < (uint64_t)max_len) ++nsteps;
+    while ((1ull << nsteps) < 64ull * (uint64_t)W) ++nsteps;
     NOALLOC_TRY(launch_eval(Wt, (const uint32_t *)(scr + o_prog), (int)prog.size(), atoms, mask, stride, plane,
                             (uint64_t *)(scr + o_stack), nsteps, (uint32_t)n_traces, d_cs_out, words_per_trace, sm));
     int invalid = 0;
@@ -135,6 +140,6 @@ extern "C" ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_le
     if (invalid)
         return set_error(LTL_ERR_INVALID,
                          "ltl_eval_noalloc: letters use propositions >= n_props, offsets decrease, or a trace is "
-                         "longer than max_len");
+                         "longer than 64 * ceil(max_len / 64) positions");
     return LTL_OK;
 }

@@ -60,3 +60,22 @@ def test_noalloc_rejects_work_beyond_the_static_scratch():
     assert rc == L.LTL_ERR_OOM
     msg = L.last_error()
     assert "static scratch" in msg and "bytes" in msg
+
+
+@pytest.mark.gpu
+def test_noalloc_trace_longer_than_max_len_within_its_words():
+    """max_len below the longest trace, but every trace within the
+    ceil(max_len / 64) words the call sizes from it: the evaluation must still
+    be exact (F, G and U reach across the whole trace), equal to ltl_eval's."""
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    ts = _rand_traces(7, 500, 3, 20, 60)          # up to 60 positions: one word
+    for formula in ("F p0", "G (p1 | p2)", "(p0 U (p1 & p2))", "X X F (p2 & X G p0)"):
+        want = L.evaluate(formula, ts, 3, words_per_trace=1)
+        d_letters = torch.from_numpy(ts.letters.astype(np.int32)).cuda()
+        d_offsets = torch.from_numpy(ts.offsets.astype(np.int64)).cuda()
+        d_out = torch.full((ts.n, 1), -1, dtype=torch.int64, device="cuda")
+        L.evaluate_noalloc(formula, d_letters, d_offsets, ts.n, 10, 3, d_out, 1)   # max_len 10 < 60
+        torch.cuda.synchronize()
+        got = d_out.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, want), formula
