@@ -245,7 +245,7 @@ static const void *cluster_fn() {
     return reinterpret_cast<const void *>(&lvl::cluster_level_kernel<W, C>);
 }
 
-// Cluster shapes: as the streaming kernel's, C * W == 8 words per thread, 256
+// Cluster shapes: as the streaming kernel's, C * W == 8 words per thread, 128
 // threads per CTA.
 const void *cluster_kernel_ptr(int W, int C) {
     switch (W * 16 + C) {

@@ -212,7 +212,7 @@ static const void *stream_fn() {
     return reinterpret_cast<const void *>(&lvl::stream_level_kernel<W, C>);
 }
 
-// Streaming shapes: C * W == 8 words per thread, 256 threads per CTA.
+// Streaming shapes: C * W == 8 words per thread, 128 threads per CTA.
 const void *stream_kernel_ptr(int W, int C) {
     switch (W * 16 + C) {
     case 1 * 16 + 8: return stream_fn<1, 8>();
