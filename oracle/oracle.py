@@ -23,11 +23,14 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ltl_oracle.c")
 LIB = os.path.join(HERE, "libltl_oracle.so")
+SRC_PAR = os.path.join(HERE, "ltl_oracle_par.c")
+LIB_PAR = os.path.join(HERE, "libltl_oracle_par.so")
 
 STATUS = {0: "found", 1: "not_found", 2: "cap", -1: "invalid", -3: "nomem", -5: "bufsize"}
 OPS_ALL = 127
 _lock = threading.Lock()
 _lib = None
+_lib_par = None
 
 
 def build(force: bool = False) -> str:
@@ -37,6 +40,35 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, SRC])
         os.replace(tmp, LIB)
     return LIB
+
+
+def build_par(force: bool = False) -> str:
+    """Compile the multi-core variant (ltl_oracle_par.c, which includes
+    ltl_oracle.c unchanged) with gcc -fopenmp."""
+    newest = max(os.path.getmtime(SRC), os.path.getmtime(SRC_PAR))
+    if force or not os.path.exists(LIB_PAR) or os.path.getmtime(LIB_PAR) < newest:
+        tmp = LIB_PAR + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, SRC_PAR])
+        os.replace(tmp, LIB_PAR)
+    return LIB_PAR
+
+
+def _load_par():
+    global _lib_par
+    with _lock:
+        if _lib_par is None:
+            build_par()
+            lib = ctypes.CDLL(LIB_PAR)
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            lib.oracle_learn_par.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                             ctypes.c_int, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                             ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int),
+                                             u64p, u64p, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+            lib.oracle_learn_par.restype = ctypes.c_int
+            _lib_par = lib
+    return _lib_par
 
 
 def _load():
@@ -153,4 +185,35 @@ def learn(P, N, n_props: int, ops: int = OPS_ALL, max_size: int = 7, stop_mode: 
         "candidates": [int(cand[c]) for c in range(K + 1)],
         "seconds": [float(secs[c]) for c in range(K + 1)],
         "levels_done": done.value,
+    }
+
+
+def learn_par(P, N, n_props: int, ops: int = OPS_ALL, max_size: int = 7, stop_mode: int = 1,
+              max_entries: int = 0, threads: int = 0, block_bytes: int = 0) -> Dict:
+    """`learn` (uniform cost, exact separation) with each block of a level's
+    candidates built on `threads` host cores (0: every core OpenMP offers) and
+    admitted in enumeration order, so every result equals `learn`'s.  The
+    returned dict also holds "threads", the team size used."""
+    letters, offsets = _concat(P, N)
+    nP, nN = P.offsets.shape[0] - 1, N.offsets.shape[0] - 1
+    K = max_size
+    uniq = (ctypes.c_uint64 * (K + 1))()
+    cand = (ctypes.c_uint64 * (K + 1))()
+    secs = (ctypes.c_double * (K + 1))()
+    fsz, done, used = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = _load_par().oracle_learn_par(letters.ctypes.data, offsets.ctypes.data, nP, nN, n_props, ops, K,
+                                      stop_mode, max_entries, int(threads), int(block_bytes), buf, len(buf),
+                                      ctypes.byref(fsz), uniq, cand, secs, ctypes.byref(done), ctypes.byref(used))
+    if rc < 0:
+        raise RuntimeError("oracle_learn_par failed: %s" % STATUS.get(rc, rc))
+    return {
+        "status": STATUS[rc],
+        "formula": buf.value.decode() if rc == 0 else None,
+        "size": fsz.value if rc == 0 else None,
+        "unique": [int(uniq[c]) for c in range(K + 1)],
+        "candidates": [int(cand[c]) for c in range(K + 1)],
+        "seconds": [float(secs[c]) for c in range(K + 1)],
+        "levels_done": done.value,
+        "threads": used.value,
     }
