@@ -16,18 +16,33 @@ Metric: candidates x traces per second = sum over completed size levels of
 
   value    traces already resident in HBM (ltl_ctx_learn_device), CUDA events
            on the library's stream around each step; L2 flushed between steps.
+           The timed region is the whole call: levels 1..6 run as one
+           device-planned chain (a CUDA graph), and between the host-planned
+           levels 7, 8 and 9 the library reads the control block back, so the
+           host's round trips are inside it.  `kernel_ms_per_step` is the sum
+           of the level launches' own device times, beside it.
   e2e      the same metric through ltl_ctx_learn with HOST trace buffers: the
            host->device copy of the traces and the device->host reads of the
            control block and formula are inside the wall-clock timed region.
-  roofline the dominant kernel (the level kernel of the largest size level):
-           algorithmic bytes / its event-timed duration vs measured HBM peak.
-  alu_roofline  the same launch: algorithmic 32-bit shift and logic operations
-           / its duration vs the integer throughput measured on the GPU.
-  cpu_baseline  the plain C oracle, single-threaded, on a bounded sample.
+  roofline the dominant kernel (the longest (size level, connective) launch):
+           algorithmic bytes with the left operand staged in shared memory --
+           the operand matrices the launch copied into shared memory (left
+           operands once per reload, counted on the device) plus one matrix
+           per candidate stored (new) or read for the full compare
+           (duplicate) -- over its event-timed duration, against the
+           measured HBM copy bandwidth; beside it the same launch's
+           algorithmic 32-bit operations against the measured integer roof
+           (alu), the count with both operands streamed, and the physical
+           DRAM bytes of an ncu capture of the same kernel sources.  `bound`
+           names the roof the launch uses the larger fraction of.
+  cpu_baseline  the oracle on the host's cores: every core (the OpenMP
+           variant, identical results) and one core (the plain C oracle), on
+           a bounded sample.
 
-`--impl reference` times the oracle alone (the CPU reference of this
-workload) with the same metric.  With torchrun (N > 1) every rank learns its
-own independent problem (seed = rank); there is no collective on the path.
+`--impl reference` times the oracle alone on every host core (the CPU
+reference of this workload) with the same metric.  With torchrun (N > 1)
+every rank learns its own independent problem (seed = rank); there is no
+collective on the path.
 """
 from __future__ import annotations
 
@@ -233,25 +248,41 @@ def autotune_summary(ctx, off):
     return {"enabled": True, "classes": chosen}
 
 
-def cpu_baseline(target_s: float = 12.0, max_size: int = 6):
-    """The oracle as it stands (single-threaded C) on the same workload,
-    sizes 1..max_size enumerated completely, repeated for ~target_s."""
-    from oracle import oracle as O
-    from paper_2402_12373_gb300 import synth
-    spec = synth.single_large()
+def _oracle_rate(learn, spec, max_size, target_s):
+    """candidates x traces per second of one oracle entry point, sizes
+    1..max_size of `spec` enumerated completely, repeated for ~target_s."""
     T = spec.n_traces
-    units = 0
-    secs = 0.0
-    runs = 0
+    units, secs, runs, used = 0, 0.0, 0, 1
     while secs < target_s or runs == 0:
         t0 = time.perf_counter()
-        r = O.learn(spec.P, spec.N, spec.n_props, max_size=max_size, stop_mode=0)
+        r = learn(spec.P, spec.N, spec.n_props, max_size=max_size, stop_mode=0)
         secs += time.perf_counter() - t0
         units += sum(r["candidates"][1:max_size + 1]) * T
         runs += 1
-    return {"value": units / secs, "unit": METRIC.split("/")[0] + "/s", "cores": 1, "kind": "oracle",
-            "sample": "single_large traces (2048), sizes 1..%d enumerated completely, %d run(s), %.1f s"
-                      % (max_size, runs, secs)}
+        used = r.get("threads", 1)
+    return units / secs, runs, secs, used
+
+
+def cpu_baseline(target_s: float = 10.0, max_size: int = 6):
+    """The oracle on the same workload, sizes 1..max_size enumerated
+    completely: on every host core (the OpenMP variant, whose results equal
+    the serial oracle's) and single-threaded (the plain C oracle)."""
+    from oracle import oracle as O
+    from paper_2402_12373_gb300 import synth
+    spec = synth.single_large()
+    sample = "single_large traces (2048), sizes 1..%d enumerated completely, %d run(s), %.1f s"
+    unit = METRIC.split("/")[0] + "/s"
+    v1, runs1, secs1, _ = _oracle_rate(O.learn, spec, max_size, target_s)
+    single = {"value": v1, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample % (max_size, runs1, secs1)}
+    try:
+        vn, runsn, secsn, used = _oracle_rate(O.learn_par, spec, max_size, target_s)
+    except Exception as e:   # no OpenMP toolchain: the single-core figure stands alone
+        single["multi_core_unavailable"] = str(e)[:200]
+        return single
+    return {"value": vn, "unit": unit, "cores": used, "kind": "oracle",
+            "sample": sample % (max_size, runsn, secsn) + " (OpenMP over each block of a level's candidates, "
+                      "admitted in enumeration order)",
+            "nproc": os.cpu_count(), "single_core": single}
 
 
 def _units_all(r, T):
@@ -400,6 +431,24 @@ def bench_trace_scaling(L, ws, spec, steps=2):
     done = r["levels_done"]
     units_done = sum(r["candidates"][1:done + 1]) * T
     units_all = sum(r["candidates"][1:]) * T
+    # the largest completed size level against the HBM roof, all of its
+    # launches together (a level of fewer than 2^17 candidates runs its
+    # connectives concurrently, so only the level has a time of its own):
+    # every candidate streams its operand matrices and stores or compares one
+    # (the kernels for matrices larger than a CTA stage no operand across
+    # candidates)
+    kd = done
+    kd_ms = statistics.mean(x["ms"][kd] for _, x in runs)
+    cm_bytes = T * 8 * r["words_per_trace"]
+    kd_bytes = sum(op_candidates(r["unique"], kd, o, spec.n_props) * ((2 if o in (2, 3, 7) else 1) + 1)
+                   for o in range(1, 8)) * cm_bytes
+    peaks, peak_src = measured_peaks()
+    ach = kd_bytes / (kd_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+            "traffic": None, "kernel": "%s, every connective of size level %d" % (
+                "stream_level_kernel" if r["candidates"][kd] >= 152 else "cluster_level_kernel", kd),
+            "candidates": r["candidates"][kd], "level_ms": kd_ms, "algorithmic_bytes": kd_bytes,
+            "peak_source": peak_src + " (hbm_gbs, copy bandwidth)"}
     return {"workload": "trace_scaling: 4 props, 32768+32768 traces, length U{33..128} (2 words per trace), "
                         "Bernoulli(0.25), every level until size 11 or a 120 GB cache budget",
             "status": r["status"], "levels_done": done, "unique": r["unique"][1:], "candidates": r["candidates"][1:],
@@ -408,7 +457,7 @@ def bench_trace_scaling(L, ws, spec, steps=2):
             "candidates_x_traces_per_s_all": units_all / (ms / 1e3),
             "launch": {"threads_per_cta": r["threads_per_cta"], "chunk_groups": r["chunk_groups"],
                        "words_per_trace": r["words_per_trace"]},
-            "entries": r["entries"], "max_entries": r["max_entries"]}
+            "entries": r["entries"], "max_entries": r["max_entries"], "roofline": roof}
 
 
 def bench_dc(L, ws, specs, windows=(16, 64)):
@@ -443,22 +492,29 @@ def run_reference(args):
     spec = synth.single_large()
     T = spec.n_traces
     K = 5
+    try:
+        learn, kind = O.learn_par, "OpenMP over each block of a level's candidates"
+        learn(spec.P, spec.N, spec.n_props, max_size=2, stop_mode=0)
+    except Exception:
+        learn, kind = O.learn, "single-threaded"
     for _ in range(args.warmup):
-        O.learn(spec.P, spec.N, spec.n_props, max_size=K, stop_mode=0)
-    units, secs = 0, 0.0
+        learn(spec.P, spec.N, spec.n_props, max_size=K, stop_mode=0)
+    units, secs, used = 0, 0.0, 1
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = O.learn(spec.P, spec.N, spec.n_props, max_size=K, stop_mode=0)
+        r = learn(spec.P, spec.N, spec.n_props, max_size=K, stop_mode=0)
         secs += time.perf_counter() - t0
         units += sum(r["candidates"][1:K + 1]) * T
+        used = r.get("threads", 1)
     value = units / secs
-    sample = "single_large traces (2048), sizes 1..%d enumerated completely per step (CPU oracle)" % K
+    sample = ("single_large traces (2048), sizes 1..%d enumerated completely per step (CPU oracle, %s)"
+              % (K, kind))
     out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
            "impl": "reference",
            "config": {"workload": WORKLOAD, "reference_sample": sample, "n_traces": T},
-           "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": METRIC, "cores": used, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
@@ -588,24 +644,31 @@ def main():
     kd, od = max(pairs, key=lambda ko: sum(r["op_ms"][ko[0]][ko[1]] for r in results))
     kd_ms = statistics.mean(r["op_ms"][kd][od] for r in results)
     per_trace = 4 if r0["traces_per_word"] == 2 else 8 * W
+    cm_bytes = T * per_trace                       # algorithmic bytes of one characteristic matrix
     n_operands = 2 if od in (2, 3, 7) else 1
     kd_cands = op_candidates(r0["unique"], kd, od, spec.n_props)
-    kd_bytes = kd_cands * (n_operands + 1) * T * per_trace
+    kd_staged = statistics.mean(r["op_staged"][kd][od] for r in results)
+    streamed_bytes = kd_cands * (n_operands + 1) * cm_bytes
+    if kd_staged > 0:
+        # operands as the kernel stages them (left operand once per reload),
+        # plus the matrix stored or read for the full compare per candidate
+        kd_bytes = (kd_staged + kd_cands) * cm_bytes
+        count = "left operand staged: operand matrices copied into shared memory (device count) + 1 per candidate"
+    else:
+        kd_bytes = streamed_bytes
+        count = "both operands streamed (this kernel reports no staged-operand count)"
     peaks, peak_src = measured_peaks()
-    achieved = kd_bytes / (kd_ms / 1e3) / 1e9
+    hbm_achieved = kd_bytes / (kd_ms / 1e3) / 1e9
+    hbm_frac = hbm_achieved / peaks["hbm_gbs"]
     sha = kernel_sources_sha()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(sha),
-                "kernel": "fused_level_kernel connective %s, size level %d (%s layout)"
-                          % (OP_NAMES[od], kd, "narrow" if r0["traces_per_word"] == 2 else "wide"),
-                "peak_source": peak_src + " (hbm_gbs, copy bandwidth)",
-                "algorithmic_bytes_per_launch": kd_bytes, "bytes_per_candidate_trace": (n_operands + 1) * per_trace,
-                "candidates_per_launch": kd_cands, "launch_ms": kd_ms,
-                "level_ms": statistics.mean(r["ms"][kd] for r in results),
-                "kernel_sources_sha": sha}
-    if roofline["traffic"]:
-        # physical DRAM bandwidth of the launch: profiled bytes over its event time
-        roofline["dram_gbs"] = roofline["traffic"] / (kd_ms / 1e3) / 1e9
+    traffic = profiled_traffic(sha)
+    kname = ("fused_level_kernel connective %s, size level %d (%s layout)"
+             % (OP_NAMES[od], kd, "narrow" if r0["traces_per_word"] == 2 else "wide"))
+    hbm = {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
+           "peak_source": peak_src + " (hbm_gbs, copy bandwidth)", "count": count,
+           "algorithmic_bytes_per_launch": kd_bytes, "operand_matrices_staged": kd_staged,
+           "matrix_bytes": cm_bytes,
+           "frac_both_operands_streamed": streamed_bytes / (kd_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
 
     # the same launch against the integer roof: algorithmic shift and logic
     # operations over the measured throughput of such operations
@@ -615,12 +678,23 @@ def main():
         ops_ct = int_ops_per_candidate_trace(od, nsteps)
         kd_ops = kd_cands * T * ops_ct
         alu_achieved = kd_ops / (kd_ms / 1e3) / 1e9
-        alu = {"bound": "alu", "achieved": alu_achieved, "peak": int_peak["ops_per_s"] / 1e9, "unit": "Gop/s",
+        alu = {"achieved": alu_achieved, "peak": int_peak["ops_per_s"] / 1e9, "unit": "Gop/s",
                "frac": alu_achieved / (int_peak["ops_per_s"] / 1e9), "ops_per_candidate_trace": ops_ct,
                "log_steps": nsteps, "algorithmic_ops_per_launch": kd_ops,
                "peak_source": "measured on this GPU (ltl_int32_peak: chains of 32-bit shifts and three-input "
-                              "logic operations, %.2f ms)" % int_peak["ms"],
-               "hbm_frac_same_launch": roofline["frac"]}
+                              "logic operations, %.2f ms)" % int_peak["ms"]}
+    # the roof the launch uses more of, by these algorithmic counts
+    main = alu if (alu is not None and alu["frac"] > hbm_frac) else hbm
+    roofline = {"bound": "alu" if main is alu else "hbm", "achieved": main["achieved"], "peak": main["peak"],
+                "unit": main["unit"], "frac": main["frac"], "traffic": traffic, "kernel": kname,
+                "candidates_per_launch": kd_cands, "launch_ms": kd_ms,
+                "level_ms": statistics.mean(r["ms"][kd] for r in results),
+                "hbm": hbm, "alu": alu, "kernel_sources_sha": sha}
+    if traffic:
+        # physical DRAM bytes of the launch (ncu, same kernel sources) over its event time
+        roofline["dram"] = {"bytes_per_launch": traffic, "gbs": traffic / (kd_ms / 1e3) / 1e9,
+                            "frac": traffic / (kd_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    kernel_ms = [sum(r["ms"][k] for k in range(1, r["levels_done"] + 1)) for r in results]
 
     # end to end: host trace buffers through ltl_ctx_learn (one untimed call
     # first: the first copy from these pageable host buffers sets up the
@@ -674,7 +748,8 @@ def main():
                        "top_level_op_ms": {name: round(statistics.mean(r["op_ms"][K][op] for r in results), 4)
                                            for op, name in enumerate(OP_NAMES) if r0["op_ms"][K][op] > 0}},
             "roofline": roofline,
-            "alu_roofline": alu,
+            "kernel_ms_per_step": statistics.mean(kernel_ms),
+            "value_by_kernel_time": local_units / (sum(kernel_ms) / 1e3),
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "time_to_learn_ms": {"median": statistics.median(ttl), "size": found["size"],
                                  "formula": found["formula"], "mode": "stop at first separator, host buffers"},

@@ -225,6 +225,13 @@ typedef struct {
                                              equal key (exact admission)       */
     uint64_t collisions;                  /* compares that found a different
                                              matrix (probing went on)          */
+    uint64_t op_staged[LTL_MAX_LEVELS][8];/* operand matrices each connective's
+                                             launch copied into shared memory
+                                             ([level][op] as op_ms): counted by
+                                             the fused level kernel on levels
+                                             planned on the host, 0 elsewhere;
+                                             a launch shared by several
+                                             problems reports its total to each */
 } ltl_stats;
 
 /* ---------------------------------------------------------------------------

@@ -80,7 +80,8 @@ class Stats(ctypes.Structure):
                 ("max_entries", ctypes.c_uint64), ("total_ms", ctypes.c_double),
                 ("op_ms", (ctypes.c_float * 8) * MAX_LEVELS),
                 ("device_planned_levels", ctypes.c_uint32), ("graph_levels", ctypes.c_uint32),
-                ("compares", ctypes.c_uint64), ("collisions", ctypes.c_uint64)]
+                ("compares", ctypes.c_uint64), ("collisions", ctypes.c_uint64),
+                ("op_staged", (ctypes.c_uint64 * 8) * MAX_LEVELS)]
 
     def to_dict(self, max_size: int) -> Dict:
         K = max_size
@@ -100,6 +101,7 @@ class Stats(ctypes.Structure):
             "op_ms": [[float(self.op_ms[c][o]) for o in range(8)] for c in range(K + 1)],
             "device_planned_levels": int(self.device_planned_levels), "graph_levels": int(self.graph_levels),
             "compares": int(self.compares), "collisions": int(self.collisions),
+            "op_staged": [[int(self.op_staged[c][o]) for o in range(8)] for c in range(K + 1)],
         }
 
 

@@ -305,6 +305,7 @@ public:
     size_t max_segs = 0;
     Problem *h_probs = nullptr;
     Ctrl *h_ctrls = nullptr;
+    unsigned long long *h_staged = nullptr;   // staged-operand counts of a round's launches
     Seg *h_segs = nullptr;
     WalkJob *h_jobs = nullptr;
     uint32_t *h_tokens = nullptr;
@@ -378,7 +379,8 @@ public:
         o_probs = take(sizeof(Problem) * max_slots);
         o_ctrls = take(sizeof(Ctrl) * max_slots);
         o_segs = take(sizeof(Seg) * max_segs);
-        o_counters = take(sizeof(unsigned long long) * kMaxGroups);
+        // tile counters of a round's launches, then their staged-operand counters
+        o_counters = take(sizeof(unsigned long long) * 2 * kMaxGroups);
         o_plan_state = take(sizeof(PlanState));
         o_plan_log = take(sizeof(PlanLog) * kMaxLevels);
         o_descs = take(sizeof(LevelDesc) * kPlanGroups);
@@ -388,6 +390,7 @@ public:
         shared_end = cur;
         LTL_CUDA_TRY(cudaMallocHost(&h_probs, sizeof(Problem) * max_slots));
         LTL_CUDA_TRY(cudaMallocHost(&h_ctrls, sizeof(Ctrl) * max_slots));
+        LTL_CUDA_TRY(cudaMallocHost(&h_staged, sizeof(unsigned long long) * kMaxGroups));
         LTL_CUDA_TRY(cudaMallocHost(&h_segs, sizeof(Seg) * max_segs));
         LTL_CUDA_TRY(cudaMallocHost(&h_jobs, sizeof(WalkJob) * max_slots));
         LTL_CUDA_TRY(cudaMallocHost(&h_tokens, sizeof(uint32_t) * kMaxTokens * max_slots));
@@ -417,13 +420,14 @@ public:
         ws = nullptr;
         if (h_probs) cudaFreeHost(h_probs);
         if (h_ctrls) cudaFreeHost(h_ctrls);
+        if (h_staged) cudaFreeHost(h_staged);
         if (h_segs) cudaFreeHost(h_segs);
         if (h_jobs) cudaFreeHost(h_jobs);
         if (h_tokens) cudaFreeHost(h_tokens);
         if (h_ntok) cudaFreeHost(h_ntok);
         if (h_plan_state) cudaFreeHost(h_plan_state);
         if (h_plan_log) cudaFreeHost(h_plan_log);
-        h_probs = nullptr; h_ctrls = nullptr; h_segs = nullptr; h_jobs = nullptr; h_tokens = nullptr; h_ntok = nullptr;
+        h_probs = nullptr; h_ctrls = nullptr; h_staged = nullptr; h_segs = nullptr; h_jobs = nullptr; h_tokens = nullptr; h_ntok = nullptr;
         h_plan_state = nullptr; h_plan_log = nullptr;
         if (ev_begin) cudaEventDestroy(ev_begin);
         if (ev_end) cudaEventDestroy(ev_end);
@@ -1083,7 +1087,7 @@ public:
         Seg *d_segs = (Seg *)(ws + o_segs);
         unsigned long long *d_counters = (unsigned long long *)(ws + o_counters);
         LTL_CUDA_TRY(cudaMemcpyAsync(d_segs, h_segs, sizeof(Seg) * n_out, cudaMemcpyHostToDevice, stream));
-        LTL_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * groups.size(), stream));
+        LTL_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 2 * kMaxGroups, stream));
         LTL_CUDA_TRY(cudaEventRecord(ev_begin, stream));
         if (concurrent)
             while ((int)aux.size() < kAuxStreams) {
@@ -1096,6 +1100,7 @@ public:
             la.segs = d_segs + first[g];
             la.probs = (const Problem *)(ws + o_probs);
             la.tile_counter = d_counters + g;
+            la.staged = d_counters + kMaxGroups + g;
             la.n_segs = (int)groups[g].seg_ids.size();
             la.total_tiles = tiles[g];
             void *args[] = {&la};
@@ -1129,6 +1134,8 @@ public:
         int hi = 0;
         for (int si : ran) hi = std::max(hi, si + 1);
         LTL_CUDA_TRY(cudaMemcpyAsync(h_ctrls, ws + o_ctrls, sizeof(Ctrl) * hi, cudaMemcpyDeviceToHost, stream));
+        LTL_CUDA_TRY(cudaMemcpyAsync(h_staged, d_counters + kMaxGroups, sizeof(unsigned long long) * groups.size(),
+                                     cudaMemcpyDeviceToHost, stream));
         LTL_CUDA_TRY(cudaStreamSynchronize(stream));
         ++total_rounds;
         // per launch: its own time when launches ran one after another; from
@@ -1155,9 +1162,10 @@ public:
                 for (int i : groups[g].seg_ids)
                     if (segs[i].prob == si) {
                         s.st.op_ms[k][groups[g].op] = op_ms[g];
+                        s.st.op_staged[k][groups[g].op] = h_staged[g];
                         break;
                     }
-            s.st.d2h_bytes += sizeof(Ctrl);
+            s.st.d2h_bytes += sizeof(Ctrl) + sizeof(unsigned long long) * groups.size();
             close_level(si, h, found_slots);
         }
         // one launch per group was shared by its problems: count it once each

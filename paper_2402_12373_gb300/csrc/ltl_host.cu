@@ -212,7 +212,7 @@ extern "C" {
 
 const char *ltl_last_error(void) { return last_error_text(); }
 
-const char *ltl_version(void) { return "ltl-gb300 0.2 (sm_103a)"; }
+const char *ltl_version(void) { return "ltl-gb300 0.3 (sm_103a)"; }
 
 ltl_status ltl_eval(const char *formula, const ltl_traces *traces, int n_props, uint64_t *cs_out,
                     int words_per_trace) {

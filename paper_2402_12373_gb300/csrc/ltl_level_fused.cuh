@@ -88,7 +88,7 @@ template <int W, int C, int NB, int OP, bool NARROW>
 __device__ __forceinline__ bool fused_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0, uint64_t a1,
                                            uint64_t b0, uint64_t b1, FusedShared<NB> &sh, uint64_t *slots,
                                            uint32_t &phase, uint32_t &round, const LaneConst &lc,
-                                           unsigned long long &done, bool cap_full) {
+                                           unsigned long long &done, unsigned long long &staged, bool cap_full) {
     constexpr bool BIN = is_binary(OP);
     const bool tri = sg.kind == SEG_TRI;
     const uint64_t *srcA = (OP == OP_ATOM) ? pb.atoms : pb.arena;
@@ -124,6 +124,7 @@ __device__ __forceinline__ bool fused_tile(const Problem &pb, int level, const S
         const bool reload_a = BIN && (a != loaded_a);
         if (lc.tid == 0) {
             const uint32_t n = (uint32_t)nb + (reload_a ? 1u : 0u);
+            staged += n;
             mbar_arrive_expect_tx(&sh.bar, n * cm_bytes);
             if (BIN) {
                 if (reload_a) bulk_g2s(slots + (uint64_t)NB * lc.stride, srcA + (sg.a_begin + a) * pb.stride, cm_bytes, &sh.bar);
@@ -411,6 +412,7 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
     // candidates of the current problem finished by this CTA, added to the
     // problem's count when the CTA moves to another problem or ends
     unsigned long long cands_acc = 0;
+    unsigned long long staged = 0;   // thread 0: operand matrices copied into shared memory
     for (;;) {
         // thread 0 takes a tile and reads its problem's stop flag
         if (lc.tid == 0) {
@@ -448,11 +450,13 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
         decode_tile(sg, tile - sg.tile_begin, a0, a1, b0, b1);
         unsigned long long done = 0;
         const bool ok =
-            fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done, cap_full);
+            fused_tile<W, C, NB, OP, NARROW>(pb, sg.level, sg, a0, a1, b0, b1, sh, slots, phase, round, lc, done, staged,
+                                             cap_full);
         cands_acc += done;
         if (!ok) break;
     }
     if (lc.tid == 0 && cands_acc) atomicAdd(&pb.ctrl->cands, cands_acc);
+    if (lc.tid == 0 && staged && la.staged) atomicAdd(la.staged, staged);
 }
 
 }  // namespace lvl

@@ -111,6 +111,8 @@ struct LevelArgs {
     int32_t pad;
     uint64_t total_tiles;
     const LevelDesc *desc;             // non-null: n_segs and total_tiles come from here
+    unsigned long long *staged;        // non-null: operand matrices the launch copied
+                                       // into shared memory are added here (fused kernel)
 };
 
 // One formula reconstruction: the provenance array of a problem, its entry
