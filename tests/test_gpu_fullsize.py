@@ -1,13 +1,19 @@
 """Parity at the full sizes of the benchmark workloads, in the launch
 configuration bench.py times (a context over a torch workspace, every level
-enumerated).  The oracle cannot redo these enumerations, so the checks are
-(a) the levels the oracle finishes in seconds, compared exactly; (b) sampled
-outputs the oracle computes one by one: cache entries of every level, rebuilt
-into formulas whose characteristic matrices the oracle evaluates and which must
-equal the stored ones, and the returned separator; (c) properties that hold at
-any size: candidate counts follow the closed form of the unique counts, every
-entry of a level has that level's size, sampled entries are pairwise distinct.
+enumerated).  The checks are (a) every level's unique and candidate counts
+equal to the oracle's, read from the JSON files that
+tests/golden/make_fullsize_levels.py writes by running the oracle alone on
+the same seeded inputs (an input digest ties each file to the generator's
+output); (b) sampled outputs the oracle computes one by one: cache entries of
+every level, rebuilt into formulas whose characteristic matrices the oracle
+evaluates and which must equal the stored ones, and the returned separator;
+(c) properties that hold at any size: candidate counts follow the closed form
+of the unique counts, every entry of a level has that level's size, sampled
+entries are pairwise distinct.
 """
+import hashlib
+import json
+import os
 import random
 
 import numpy as np
@@ -20,6 +26,22 @@ import ltl_ref as R
 from oracle import oracle as O
 from paper_2402_12373_gb300 import _lib as L
 from paper_2402_12373_gb300 import synth
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_levels(name, spec):
+    """The oracle's per-level counts for workload `name`, after checking that
+    they were computed on exactly these inputs."""
+    with open(os.path.join(GOLDEN, "%s_levels.json" % name)) as f:
+        g = json.load(f)
+    h = hashlib.sha256()
+    for ts in (spec.P, spec.N):
+        h.update(np.ascontiguousarray(ts.letters, dtype=np.uint32).tobytes())
+        h.update(np.ascontiguousarray(ts.offsets, dtype=np.uint64).tobytes())
+    assert h.hexdigest() == g["input_sha256"], "generated inputs differ from the golden file's"
+    return g
 
 
 def _oracle_words(formula, traces, n_props, W):
@@ -56,9 +78,10 @@ def test_single_large_full_size():
         got = ctx.learn(s.P, s.N, 3, max_size=9)
         assert got["levels_done"] == 9 and got["status"] == "found" and got["size"] == 8
         assert O.separates(got["formula"], s.P, s.N, 3)
-        want = O.learn(s.P, s.N, 3, max_size=6, stop_mode=0)
-        assert got["unique"][1:7] == want["unique"][1:7]
-        assert got["candidates"][1:7] == want["candidates"][1:7]
+        want = _golden_levels("single_large", s)      # the oracle, every level 1..9
+        assert want["max_size"] == 9 and want["levels_done"] == 9 and want["size"] == 8
+        assert got["unique"][1:10] == want["unique"][1:10]
+        assert got["candidates"][1:10] == want["candidates"][1:10]
         cc = R.candidate_counts(got["unique"], L.ALL, 9)
         assert got["candidates"][2:10] == cc[2:10]
         both = synth.TraceSet.from_list(s.P.to_list() + s.N.to_list())
@@ -79,16 +102,18 @@ def test_single_large_full_size_time_to_learn_mode():
 def test_trace_scaling_full_size():
     """65536 traces of length 33..128 (two words, two-pass streaming kernel)."""
     s = synth.trace_scaling()
-    ws = L.default_workspace(16 << 30)
+    want = _golden_levels("trace_scaling", s)         # the oracle, every level 1..K
+    K = want["max_size"]
+    ws = L.default_workspace(24 << 30)
     with L.Context(workspace=ws, stop=L.STOP_NONE) as ctx:
-        got = ctx.learn(s.P, s.N, 4, max_size=4)
+        got = ctx.learn(s.P, s.N, 4, max_size=K)
         assert got["words_per_trace"] == 2 and got["chunk_groups"] > 1
-        want = O.learn(s.P, s.N, 4, max_size=3, stop_mode=0)
-        assert got["unique"][1:4] == want["unique"][1:4]
-        assert got["candidates"][1:4] == want["candidates"][1:4]
-        cc = R.candidate_counts(got["unique"], L.ALL, 4)
-        assert got["candidates"][2:5] == cc[2:5]
-        assert got["status"] == "found" and got["size"] == want["size"] == 3
+        assert got["levels_done"] == want["levels_done"] == K
+        assert got["unique"][1:K + 1] == want["unique"][1:K + 1]
+        assert got["candidates"][1:K + 1] == want["candidates"][1:K + 1]
+        cc = R.candidate_counts(got["unique"], L.ALL, K)
+        assert got["candidates"][2:K + 1] == cc[2:K + 1]
+        assert got["status"] == want["status"] == "found" and got["size"] == want["size"] == 3
         assert O.separates(got["formula"], s.P, s.N, 4)
         both = synth.TraceSet.from_list(s.P.to_list() + s.N.to_list())
-        _check_sampled_entries(ctx, got, both, 4, 4, 3, 2)
+        _check_sampled_entries(ctx, got, both, 4, K, 2, 2)
