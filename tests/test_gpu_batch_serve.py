@@ -2,7 +2,14 @@
 advanced in rounds, launches shared between problems) give every problem the
 result it gets alone: the same status, minimal size, completed levels and
 per-level unique and candidate counts; the returned formula separates under
-the oracle's semantics.  Counts are integers, so the comparison is exact."""
+the oracle's semantics.  Counts are integers, so the comparison is exact.
+
+The problems of the batched workload itself (a fixed slice of
+synth.batched_problem) and of the served workload (trace-scaling problems of
+the served pool's seeds) are also compared with the oracle directly: status,
+minimal size, completed levels and every completed level's counts."""
+import concurrent.futures
+import multiprocessing
 import random
 import time
 
@@ -116,3 +123,104 @@ def test_server_alone_vs_mix(ws):
     for i, (P, N, n_props, ops, K) in enumerate(problems):
         _same(alone[i], results[i], K)
         assert results[i]["latency_ms"] >= results[i]["queue_ms"] >= 0.0
+
+
+# A fixed slice of the batched workload's own problems (synth.batched_problem,
+# base seed 0) that the oracle solves in seconds: 34..6960 traces, 2..5
+# propositions, minimal sizes 1..7, max size = planted size + 2.
+BATCH_SLICE = [0, 1, 2, 3, 4, 5, 8, 10, 11, 15, 16, 22, 23, 30, 36, 37, 38, 40, 44, 45, 49, 50, 51, 56,
+               59, 63]
+# Seeds of the served workload's trace-scaling problems (65536 traces each).
+SERVED_SEEDS = [1000, 1001, 1002, 1003]
+
+
+def _spec(kind, i):
+    return synth.batched_problem(i) if kind == "batched" else synth.trace_scaling(i)
+
+
+def _max_size(kind, sp):
+    return sp.planted_size + 2 if kind == "batched" else 11
+
+
+def _oracle_job(kind, i):
+    """Oracle result (stop at the first separator) of one problem; runs in a
+    spawn-started worker process."""
+    from oracle import oracle as Oc
+    sp = _spec(kind, i)
+    return Oc.learn(sp.P, sp.N, sp.n_props, max_size=_max_size(kind, sp), stop_mode=1)
+
+
+@pytest.fixture(scope="module")
+def oracle_results():
+    jobs = [("batched", i) for i in BATCH_SLICE] + [("served", s) for s in SERVED_SEEDS]
+    with concurrent.futures.ProcessPoolExecutor(max_workers=8,
+                                                mp_context=multiprocessing.get_context("spawn")) as ex:
+        futs = {j: ex.submit(_oracle_job, *j) for j in jobs}
+        return {j: f.result() for j, f in futs.items()}
+
+
+def _equals_oracle(got, want, sp):
+    assert got["status"] == want["status"], (got["status"], want["status"])
+    assert got["size"] == want["size"]
+    d = want["levels_done"]
+    assert got["levels_done"] == d
+    assert got["unique"][1:d + 1] == want["unique"][1:d + 1]
+    assert got["candidates"][1:d + 1] == want["candidates"][1:d + 1]
+    if got["status"] == "found":
+        assert O.separates(got["formula"], sp.P, sp.N, sp.n_props), got["formula"]
+        assert O.size(got["formula"]) == got["size"]
+
+
+def _budgets(ws, specs):
+    """Per-problem memory budgets proportional to the trace counts (as in the
+    benchmark), at least 64 MiB so that no problem of the slice fills its cache
+    before the oracle's minimal size."""
+    T = [sp.n_traces for sp in specs]
+    return [max(64 << 20, int(0.5 * ws.numel() * t / sum(T))) for t in T]
+
+
+def test_batched_workload_slice_equals_oracle(ws, oracle_results):
+    """The batched workload's problems through one ltl_learn_batch call, with
+    budgets proportional to their trace counts as in the benchmark."""
+    specs = [_spec("batched", i) for i in BATCH_SLICE]
+    budgets = _budgets(ws, specs)
+    items = [(sp.P, sp.N, sp.n_props, L.ALL, _max_size("batched", sp), b) for sp, b in zip(specs, budgets)]
+    batch = L.learn_batch(items, stop=L.STOP_FIRST, workspace=ws)
+    for i, sp, got in zip(BATCH_SLICE, specs, batch):
+        _equals_oracle(got, oracle_results[("batched", i)], sp)
+
+
+def _serve(ws, specs, kind, budgets, stagger):
+    with L.Server(workspace=ws, stop=L.STOP_FIRST, max_resident=64) as srv:
+        ids, results = {}, {}
+        for n, sp in enumerate(specs):
+            ids[srv.submit(sp.P, sp.N, sp.n_props, max_size=_max_size(kind, sp), budget=budgets[n])] = n
+            if n % stagger == stagger - 1:   # requests arrive while others run
+                time.sleep(0.002)
+                for r in srv.poll(64, 0):
+                    results[ids[r["id"]]] = r
+        t0 = time.time()
+        while len(results) < len(specs) and time.time() - t0 < 300:
+            for r in srv.poll(64, 100):
+                results[ids[r["id"]]] = r
+        assert srv.pending() == (0, 0)
+    assert len(results) == len(specs)
+    return [results[n] for n in range(len(specs))]
+
+
+def test_served_batched_slice_equals_oracle(ws, oracle_results):
+    specs = [_spec("batched", i) for i in BATCH_SLICE]
+    got = _serve(ws, specs, "batched", _budgets(ws, specs), 4)
+    for i, sp, r in zip(BATCH_SLICE, specs, got):
+        _equals_oracle(r, oracle_results[("batched", i)], sp)
+
+
+def test_served_trace_scaling_requests_equal_oracle(oracle_results):
+    """Config-5-shaped requests (65536 two-word traces each, 2 GiB per
+    problem as in the benchmark) through the continuous-batching server."""
+    big = L.default_workspace(12 << 30)
+    specs = [_spec("served", s) for s in SERVED_SEEDS]
+    got = _serve(big, specs, "served", [2 << 30] * len(specs), 2)
+    for s, sp, r in zip(SERVED_SEEDS, specs, got):
+        _equals_oracle(r, oracle_results[("served", s)], sp)
+    del big
