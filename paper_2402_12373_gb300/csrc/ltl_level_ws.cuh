@@ -1,37 +1,35 @@
 // ltl_level_ws.cuh -- the size-level candidate kernel with warp-specialised
-// hash probes (for matrices that fit in one CTA's registers).
+// hash warps (for matrices that fit in one CTA's registers).
 //
 // The same per-candidate work as the fused kernel (ltl_level_fused.cuh), but
-// the hash-set probe of a batch no longer stalls the arithmetic:
+// no compute thread ever waits for a global-memory round trip of the hash set:
 //
 //   * NT compute threads pull tiles, receive each batch's operands in shared
 //     memory by TMA bulk copies (prefetched one batch ahead), compute the NB
 //     candidates in registers (exponential propagation, Section 4) and stage
 //     them -- with per-warp NH fingerprint partial sums and misclassification
-//     counts -- in a ring slot in shared memory.  While the slot's hash warp
-//     probes that batch, they compute the next one; then they store the new
-//     matrices of the probed batch into the cache, or compare its duplicates
-//     word by word with the stored entries, each thread on its own share.
-//   * Two hash warps, one per ring slot: lane k sums the partials of
-//     candidate k, records a separator (eq. (dagger), or the noisy variant)
-//     and probes the device hash set; after the compute threads' stores and
-//     compares it publishes new entries.  Candidates left unsettled (another
-//     CTA's unpublished entry, a key shared within the batch, a fingerprint
-//     collision) are finished by the hash warp alone from the ring slot.
+//     counts -- in a ring slot in shared memory, then go on with the next
+//     batch.
+//   * Two hash warps, one per ring slot, settle a staged batch completely:
+//     lane k sums the partials of candidate k, records a separator (eq.
+//     (dagger), or the noisy variant) and probes the device hash set; the warp
+//     then copies the new matrices from the ring slot into the cache (every
+//     lane a share of each matrix), compares duplicates with the stored entries
+//     (two matrices' worth of 16-byte loads in flight per lane), publishes the
+//     new entries and probes on for fingerprint collisions, before freeing the
+//     slot.
 //
-// Slots hand over through mbarriers: full (batch staged), decided (first
-// probe round done), stored (stores and compares done), empty (slot free).
-// Every wait is bounded; a timed-out wait is made the same in every compute
-// thread (barrier reduction) before anyone acts on it, sets the problem's
-// error flag and winds the kernel down.
+// Slots hand over through two mbarriers: full (batch staged, compute -> hash)
+// and empty (slot free, hash -> compute).  Every wait is bounded; a timed-out
+// wait in the compute threads is made the same in every compute thread
+// (barrier reduction) before anyone acts on it, sets the problem's error flag
+// and winds the kernel down.
 //
 // Progress: a probe never blocks on another CTA's unpublished entry (DEC_WAIT
-// is retried in a later round), and no claim's publication waits on another
-// CTA.  A claim of a first probe round is published once the compute threads
-// have stored its matrix, which they do right after computing the next batch
-// and before waiting for a free slot; a claim of a later round is stored and
-// published by the hash warp itself in that round.  So every entry a hash
-// warp waits for is published without depending on that warp.
+// is retried in a later round), and a hash warp stores and publishes the
+// entries it claims in the same round, before it can wait on anything.  So
+// every entry a hash warp waits for is published without depending on that
+// warp, and nothing a hash warp does waits on the compute threads.
 #pragma once
 #include "ltl_level_common.cuh"
 
@@ -109,8 +107,7 @@ __device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, un
     return true;
 }
 
-// What the compute threads leave in a ring slot for its hash warp, and the
-// hash warp's decisions for the compute threads.
+// What the compute threads leave in a ring slot for its hash warp.
 template <int NB>
 struct SlotMeta {
     unsigned long long fp[kMaxCWarps][NB];   // per compute warp: NH partial sums
@@ -118,18 +115,13 @@ struct SlotMeta {
     int prob;                                // problem index; -1: no more batches
     int level;
     int nb;                                  // candidates in the batch
-    uint32_t neq;                            // compute -> hash: duplicates that differ (bit k)
     uint64_t pa, pb;                         // provenance base: left operand, first right operand
-    int dec[NB];                             // hash -> compute: DEC_NEW (store), DEC_CMP (compare), else nothing
-    unsigned long long idx[NB];              // the entry to store into or compare with
 };
 
 template <int NB>
 struct WsShared {
     SlotMeta<NB> meta[kRing];
     alignas(8) uint64_t full[kRing];      // batch staged (compute -> hash)
-    alignas(8) uint64_t decided[kRing];   // first probe round done (hash -> compute)
-    alignas(8) uint64_t stored[kRing];    // stores and compares done (compute -> hash)
     alignas(8) uint64_t empty[kRing];     // slot free again (hash -> compute)
     alignas(8) uint64_t ops;
     unsigned long long tile;
@@ -182,41 +174,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
     Problem pb;
     bool alive = true;
     bool inflight = false;   // operand copies issued and not yet waited for
-    bool pending = false;    // a handed-over batch whose stores and compares are still to do
     uint64_t *ring = nullptr;
-    // Stores (DEC_NEW) and compares (DEC_CMP) of the batch in ring slot `ps`,
-    // once its hash warp has decided, by every compute thread on its own share
-    // of each matrix; then the hash warp publishes.
-    auto finish = [&](int ps, uint32_t use) {
-        if (!compute_all(lc.nt, mbar_wait_for(&sh.decided[ps], use & 1u, pb.spin_limit))) {
-            if (lc.tid == 0) {
-                atomicCAS(&pb.ctrl->err, 0, -4 /* LTL_ERR_TIMEOUT */);
-                atomicExch(&pb.ctrl->stop, 1);
-            }
-            alive = false;
-            return;
-        }
-        SlotMeta<NB> &mt = sh.meta[ps];
-        const uint64_t *cms = ring + (uint64_t)ps * NB * lc.stride;
-        // the batch may belong to another problem of the launch than the
-        // current tile: its cache is looked up from its own problem index
-        uint64_t *arena = la.probs[mt.prob].arena;
-        uint32_t neq = 0;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            if (k >= mt.nb) break;
-            const int d = mt.dec[k];
-            if (d != DEC_NEW && d != DEC_CMP) continue;
-            Frag<W, C> v;
-            load_frag<W, C, false>(cms + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, v);
-            uint64_t *ent = arena + mt.idx[k] * lc.stride;
-            if (d == DEC_NEW) store_frag<W, C>(v, ent, lc.plane, lc.toff, lc.cs);
-            else if (!equal_frag<W, C>(v, ent, lc.plane, lc.toff, lc.cs)) neq |= 1u << k;
-        }
-        neq = __reduce_or_sync(0xffffffffu, neq);
-        if (lc.lane == 0 && neq) atomicOr(&mt.neq, neq);
-        mbar_arrive(&sh.stored[ps]);
-    };
     // a timed-out wait (same outcome in every compute thread) stops the launch's work
     auto give_up = [&]() {
         if (lc.tid == 0) {
@@ -319,16 +277,29 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
             Frag<W, C> r[NB];
             uint64_t fp[NB];
             uint32_t errs[NB];
+            if constexpr (OP == OP_U) {
+                // the batch shares its left operand (slot NB); slots k >= nb
+                // hold an earlier batch's operands, computed and then ignored
+                Frag<W, C> x;
+                load_frag<W, C, false>(opslots + (uint64_t)NB * lc.stride, lc.plane, lc.toff, lc.cs, x);
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+                    load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
+                apply_binary_batch<OP, W, C, NB, NARROW>(r, x, pb.nsteps);
+            }
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
                 fp[k] = 0;
                 errs[k] = 0;
                 if (k < nb) {
-                    Frag<W, C> x, m;
-                    load_frag<W, C, false>(opslots + (uint64_t)(BIN ? NB : k) * lc.stride, lc.plane, lc.toff, lc.cs, x);
-                    if (BIN) load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
-                    if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
-                    apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps);
+                    if constexpr (OP != OP_U) {
+                        Frag<W, C> x, m;
+                        load_frag<W, C, false>(opslots + (uint64_t)(BIN ? NB : k) * lc.stride, lc.plane, lc.toff,
+                                               lc.cs, x);
+                        if (BIN) load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
+                        if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
+                        apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps);
+                    }
                     const uint32_t bits = pos0_bits<W, C, NARROW>(r[k]);
                     errs[k] = (uint32_t)__popc((bits ^ lc.want) & lc.care);
                 }
@@ -367,17 +338,6 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
                 for (int off = 16; off > 0; off >>= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], off);
                 errs[k] = __reduce_add_sync(0xffffffffu, errs[k]);
             }
-            // first the stores and compares of the previous batch, probed while
-            // this one was computed: its hash warp then publishes its claims.
-            // This comes before waiting for a free slot, so that publishing a
-            // claim never waits on anything (a hash warp finishing a batch in
-            // its slow path may wait for another CTA's claims; those must not,
-            // in turn, wait for this CTA's slots)
-            if (pending) {
-                finish((int)((batch - 1) & 1u), (batch - 1) >> 1);
-                if (!alive) break;
-                pending = false;
-            }
             // hand the batch to the slot's hash warp
             const int slot = (int)(batch & 1u);
             if (!compute_all(lc.nt, mbar_wait_for(&sh.empty[slot], ((batch >> 1) & 1u) ^ 1u, pb.spin_limit))) {
@@ -404,12 +364,10 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
                 mt.pb = BIN ? sg.b_begin + cur_bf : 0;
             }
             mbar_arrive(&sh.full[slot]);
-            pending = true;
             ++batch;
         }
         if (!alive) break;
     }
-    if (pending && alive) finish((int)((batch - 1) & 1u), (batch - 1) >> 1);
     // a wait that gave up may leave this CTA's own operand copies in flight:
     // wait for them (bounded) before the CTA's shared memory goes away
     if (inflight) compute_all(lc.nt, mbar_wait_for(&sh.ops, ops_phase, 1ull << 26));
@@ -456,6 +414,53 @@ __device__ __forceinline__ int probe_round(const Problem &pb, int lane, int nb_m
         }
     }
     return dec;
+}
+
+// One matrix from a ring slot (shared memory) into its cache entry, the
+// warp's 32 lanes 16 bytes apart, 16 stores in flight per lane.
+__device__ __forceinline__ void copy_matrix(const uint64_t *src, uint64_t *dst, uint64_t stride, int lane) {
+    constexpr int kU = 8;
+    for (uint64_t base = 2 * (uint64_t)lane; base < stride; base += 64 * kU) {
+        ulonglong2 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (base + 64 * u < stride) v[u] = *reinterpret_cast<const ulonglong2 *>(src + base + 64 * u);
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (base + 64 * u < stride) *reinterpret_cast<ulonglong2 *>(dst + base + 64 * u) = v[u];
+    }
+}
+
+// Full compare of two staged matrices with two cache entries (k0 may equal k1
+// for a single one): both entries' loads are issued before any is used, so a
+// pair costs one global round trip per 16 KiB of the two.  Entries published
+// during this launch are read through L2 only (ld.cg).  Returns the bits k of
+// the candidates whose matrix differs.
+__device__ __forceinline__ uint32_t compare_two(const uint64_t *s0, const uint64_t *e0, const uint64_t *s1,
+                                                const uint64_t *e1, uint64_t stride, int lane, int k0, int k1) {
+    constexpr int kU = 8;
+    bool eq0 = true, eq1 = true;
+    for (uint64_t base = 2 * (uint64_t)lane; base < stride; base += 64 * kU) {
+        ulonglong2 q0[kU], q1[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (base + 64 * u < stride) {
+                q0[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(e0 + base + 64 * u));
+                q1[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(e1 + base + 64 * u));
+            }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (base + 64 * u < stride) {
+                const ulonglong2 v0 = *reinterpret_cast<const ulonglong2 *>(s0 + base + 64 * u);
+                const ulonglong2 v1 = *reinterpret_cast<const ulonglong2 *>(s1 + base + 64 * u);
+                eq0 &= (q0[u].x == v0.x) & (q0[u].y == v0.y);
+                eq1 &= (q1[u].x == v1.x) & (q1[u].y == v1.y);
+            }
+    }
+    uint32_t neq = 0;
+    if (__any_sync(0xffffffffu, !eq0)) neq |= 1u << k0;
+    if (__any_sync(0xffffffffu, !eq1)) neq |= 1u << k1;
+    return neq;
 }
 
 template <int NB, int OP>
@@ -511,82 +516,34 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             key = admission_key(pb, s, h);
             state = S_PROBE;
         }
-        // first round; the compute threads store and compare what it decided
-        const bool cap_full = __shfl_sync(0xffffffffu, lane == 0 ? ld_volatile_i32(&pb.ctrl->cap_hit) : 0, 0) != 0;
-        probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
-        if (lane < NB) {
-            mt.dec[lane] = state == S_STORE ? DEC_NEW : state == S_CMP ? DEC_CMP : DEC_DUP;
-            mt.idx[lane] = idx;
-        }
-        if (lane == 0) mt.neq = 0u;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.decided[slot]);
-        if (!wait_all(&sh.stored[slot], uses & 1u)) {
-            flush();
-            return;
-        }
-        const uint32_t neq0 = mt.neq;
-        {
-            const uint32_t mcmp = __ballot_sync(0xffffffffu, state == S_CMP);
-            if (lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
-        }
-        if (state == S_STORE) {
-            pb.prov[idx] = prov;
-            st_release_u32(pb.hvals + h, (uint32_t)idx);
-            state = S_DONE;
-        } else if (state == S_CMP) {
-            if ((neq0 >> lane) & 1u) {   // same fingerprint, different matrix
-                atomicAdd(&pb.ctrl->collisions, 1ull);
-                h = (h + 1) & pb.hmask;
-                state = S_PROBE;
-            } else {
-                state = S_DONE;
-            }
-        }
-        // rare: candidates still unsettled (another CTA's unpublished entry,
-        // a key shared within the batch, a collision) are finished by this
-        // warp alone from the ring slot
+        // every round: probe the unsettled lanes, copy the new matrices into
+        // the cache, compare the duplicates, publish, probe on after a
+        // collision (a round that met another CTA's unpublished entry is
+        // retried after a short sleep)
         while (__any_sync(0xffffffffu, state != S_DONE)) {
-            const int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, ld_volatile_i32(&pb.ctrl->cap_hit) != 0);
+            const bool cap_full =
+                __shfl_sync(0xffffffffu, lane == 0 ? ld_volatile_i32(&pb.ctrl->cap_hit) : 0, 0) != 0;
+            const int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
             const uint32_t m_store = __ballot_sync(0xffffffffu, state == S_STORE);
             const uint32_t m_cmp = __ballot_sync(0xffffffffu, state == S_CMP);
-            uint32_t neq = 0;
-            for (uint32_t m = m_store | m_cmp; m; m &= m - 1) {
+            for (uint32_t m = m_store; m; m &= m - 1) {
                 const int k = __ffs(m) - 1;
                 const unsigned long long ik = __shfl_sync(0xffffffffu, idx, k);
-                const uint64_t *src = cms + (uint64_t)k * pb.stride;
-                uint64_t *ent = pb.arena + ik * pb.stride;
-                constexpr int kUnroll = 8;   // 16-byte pieces in flight per lane
-                if ((m_store >> k) & 1u) {
-                    for (uint64_t base = 2 * (uint64_t)lane; base < pb.stride; base += 64 * kUnroll) {
-                        ulonglong2 v[kUnroll];
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u)
-                            if (base + 64 * u < pb.stride)
-                                v[u] = *reinterpret_cast<const ulonglong2 *>(src + base + 64 * u);
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u)
-                            if (base + 64 * u < pb.stride) *reinterpret_cast<ulonglong2 *>(ent + base + 64 * u) = v[u];
-                    }
-                } else {
-                    bool eq = true;
-                    for (uint64_t base = 2 * (uint64_t)lane; base < pb.stride; base += 64 * kUnroll) {
-                        ulonglong2 q[kUnroll];
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u)
-                            if (base + 64 * u < pb.stride)
-                                q[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(ent + base + 64 * u));
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u)
-                            if (base + 64 * u < pb.stride) {
-                                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src + base + 64 * u);
-                                eq &= (q[u].x == v.x) & (q[u].y == v.y);
-                            }
-                    }
-                    if (__any_sync(0xffffffffu, !eq)) neq |= 1u << k;
-                }
+                copy_matrix(cms + (uint64_t)k * pb.stride, pb.arena + ik * pb.stride, pb.stride, lane);
             }
-            __syncwarp();
+            uint32_t neq = 0;
+            for (uint32_t m = m_cmp; m;) {
+                const int k0 = __ffs(m) - 1;
+                m &= m - 1;
+                const int k1 = m ? __ffs(m) - 1 : k0;
+                if (m) m &= m - 1;
+                const unsigned long long i0 = __shfl_sync(0xffffffffu, idx, k0);
+                const unsigned long long i1 = __shfl_sync(0xffffffffu, idx, k1);
+                neq |= compare_two(cms + (uint64_t)k0 * pb.stride, pb.arena + i0 * pb.stride,
+                                   cms + (uint64_t)k1 * pb.stride, pb.arena + i1 * pb.stride, pb.stride, lane, k0,
+                                   k1);
+            }
+            __syncwarp();   // every lane's share of the new matrices is written
             {
                 const uint32_t mcmp = __ballot_sync(0xffffffffu, state == S_CMP);
                 if (lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
@@ -596,7 +553,7 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                 st_release_u32(pb.hvals + h, (uint32_t)idx);
                 state = S_DONE;
             } else if (state == S_CMP) {
-                if ((neq >> lane) & 1u) {
+                if ((neq >> lane) & 1u) {   // same fingerprint, different matrix
                     atomicAdd(&pb.ctrl->collisions, 1ull);
                     h = (h + 1) & pb.hmask;
                     state = S_PROBE;
@@ -628,8 +585,6 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) ws_level_kernel(
     if (tid == 0) {
         for (int s = 0; s < ws::kRing; ++s) {
             ws::mbar_init(&sh.full[s], (uint32_t)nt);
-            ws::mbar_init(&sh.decided[s], 1);
-            ws::mbar_init(&sh.stored[s], (uint32_t)nt);
             ws::mbar_init(&sh.empty[s], 1);
         }
         ws::mbar_init(&sh.ops, 1);
