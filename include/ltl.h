@@ -154,9 +154,11 @@ typedef struct {
 
 /* level_kernel values.  All kernels compute the same candidates, counts and
  * cache; they differ in how the check-and-cache step is scheduled.
- *   LTL_KERNEL_AUTO   the fused kernel for matrices that fit one CTA (on the
- *                     workloads measured it runs as fast as the
- *                     warp-specialised one with less shared memory); for
+ *   LTL_KERNEL_AUTO   for matrices that fit one CTA, per launch: the
+ *                     warp-specialised kernel when the problem's round has at
+ *                     least 2^15 candidates and the shape's ring fits shared
+ *                     memory, the fused kernel otherwise (small rounds are
+ *                     bound by launch latency); for
  *                     larger matrices, rounds with fewer candidates than SMs
  *                     run the cluster kernel (a thread-block cluster holds one
  *                     candidate in its CTAs' shared memory) when a slice
@@ -166,9 +168,10 @@ typedef struct {
  *                     larger matrices by the two-pass streaming kernel
  *   LTL_KERNEL_WS     compute warps hand each batch to dedicated hash warps
  *                     through a shared-memory ring and compute the next one
- *                     while it is probed (when the ring fits in shared
- *                     memory; else the fused kernel); larger matrices by the
- *                     cluster kernel in every round (when a slice fits) */
+ *                     while the hash warps probe, store and compare it (when
+ *                     the ring fits in shared memory; else the fused kernel),
+ *                     in every launch; larger matrices by the cluster kernel
+ *                     in every round (when a slice fits) */
 enum { LTL_KERNEL_AUTO = 0, LTL_KERNEL_FUSED = 1, LTL_KERNEL_WS = 2 };
 
 /* level_planning values.  A level's candidate space (Section 3) depends on how
@@ -228,8 +231,9 @@ typedef struct {
     uint64_t op_staged[LTL_MAX_LEVELS][8];/* operand matrices each connective's
                                              launch copied into shared memory
                                              ([level][op] as op_ms): counted by
-                                             the fused level kernel on levels
-                                             planned on the host, 0 elsewhere;
+                                             the fused and warp-specialised
+                                             level kernels on levels planned
+                                             on the host, 0 elsewhere;
                                              a launch shared by several
                                              problems reports its total to each */
 } ltl_stats;

@@ -53,7 +53,9 @@ struct Layout {
     int block = 0;          // threads per CTA: NT, plus the hash warps of the warp-specialised kernel
     int CL = 0;             // CTAs per cluster of the cluster kernel (0: not used)
     bool narrow = false;
-    bool ws = false;        // warp-specialised level kernel
+    bool ws = false;        // warp-specialised level kernel for every launch (on request)
+    bool ws_ok = false;     // the warp-specialised kernel exists for this shape and its ring fits
+    size_t ws_smem = 0;     // its dynamic shared memory
     uint32_t G = 0;
     uint32_t n_traces = 0, n_pos = 0;
     int n_props = 0, nsteps = 0;
@@ -149,6 +151,9 @@ struct FreeList {
 // Dynamic shared memory the warp-specialised kernel may take: what is left
 // of the opt-in maximum (227 KB) after its static part, rounded down.
 constexpr size_t kWsSmemMax = 224 * 1024;
+// A problem's round of at least this many candidates runs the
+// warp-specialised kernel under LTL_KERNEL_AUTO (when its shape has one).
+constexpr uint64_t kWsAutoMin = 1ull << 15;
 // Shared memory one CTA of the cluster kernel may hold its slice in.
 constexpr size_t kClusterSliceMax = 200 * 1024;
 
@@ -227,8 +232,10 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
     // own compiled batch size)
     const int ws_nb = L.G == 1 ? ws_kernel_batch(L.Wt, L.C, L.narrow) : 1;
     const size_t ws_smem = (size_t)(3 * ws_nb + 1) * 8 * L.stride;
-    // on request, any shape whose ring fits; the automatic choice is the
-    // fused kernel (as fast on the measured workloads, less shared memory)
+    L.ws_smem = ws_smem;
+    L.ws_ok = L.G == 1 && ws_nb == L.NB && ws_smem <= kWsSmemMax;
+    // on request, any shape whose ring fits, for every launch; the automatic
+    // choice takes it per launch (large rounds, see round())
     const bool want_ws = level_kernel == LTL_KERNEL_WS;
     if (L.G == 1 && want_ws && ws_smem <= kWsSmemMax) {
         L.ws = true;
@@ -496,11 +503,13 @@ public:
         return n;
     }
 
+    static const void *ws_kernel_for(const Layout &L, int op) {
+        if (L.narrow) return ws_kernel_ptr_narrow(L.C, op);
+        return L.Wt == 1 ? ws_kernel_ptr_w1(L.C, op) : ws_kernel_ptr_wn(L.Wt, L.C, op);
+    }
+
     const void *kernel_for(const Layout &L, int op) const {
-        if (L.ws) {
-            if (L.narrow) return ws_kernel_ptr_narrow(L.C, op);
-            return L.Wt == 1 ? ws_kernel_ptr_w1(L.C, op) : ws_kernel_ptr_wn(L.Wt, L.C, op);
-        }
+        if (L.ws) return ws_kernel_for(L, op);
         if (L.narrow) return fused_kernel_ptr_narrow(L.C, op);
         return L.G == 1 ? fused_kernel_ptr(L.Wt, L.C, op) : stream_kernel_ptr(L.Wt, L.C);
     }
@@ -1000,7 +1009,8 @@ public:
             int nt, op, nb;
             size_t smem;
             std::vector<int> seg_ids;
-            int cl = 0;   // cluster size of the cluster kernel
+            int cl = 0;        // cluster size of the cluster kernel
+            bool ws = false;   // the warp-specialised kernel
         };
         std::vector<Group> groups;
         // Matrices larger than one CTA: the cluster kernel (one candidate over
@@ -1010,18 +1020,27 @@ public:
         // every SM has candidates of its own).
         std::vector<uint64_t> prob_cands(max_slots, 0);
         for (const Seg &sg : segs) prob_cands[sg.prob] += seg_candidates(sg);
+        // Matrices that fit one CTA: the warp-specialised kernel (hash warps
+        // settle batches while the compute warps go on) for a problem whose
+        // round has at least kWsAutoMin candidates, the fused kernel for the
+        // smaller rounds, which are bound by launch and drain latency.
         for (int i = 0; i < (int)segs.size(); ++i) {
             const Slot &s = slots[segs[i].prob];
             const bool cluster =
                 s.L.CL > 0 && (opts.level_kernel == LTL_KERNEL_WS || prob_cands[segs[i].prob] < (uint64_t)n_sm);
-            const void *fn = cluster ? cluster_kernel_ptr(s.L.Wt, s.L.C) : kernel_for(s.L, segs[i].op);
+            const bool auto_ws = !cluster && !s.L.ws && s.L.ws_ok && opts.level_kernel == LTL_KERNEL_AUTO &&
+                                 prob_cands[segs[i].prob] >= kWsAutoMin;
+            const void *fn = cluster   ? cluster_kernel_ptr(s.L.Wt, s.L.C)
+                             : auto_ws ? ws_kernel_for(s.L, segs[i].op)
+                                       : kernel_for(s.L, segs[i].op);
             const int cl = cluster ? s.L.CL : 0;
-            const size_t smem = cluster ? s.L.smem : (s.L.CL ? 0 : s.L.smem);
+            const int nt = auto_ws ? s.L.NT + kWsExtraThreads : s.L.block;
+            const size_t smem = cluster ? s.L.smem : (s.L.CL ? 0 : (auto_ws ? s.L.ws_smem : s.L.smem));
             int g = -1;
             for (int j = 0; j < (int)groups.size(); ++j)
-                if (groups[j].fn == fn && groups[j].nt == s.L.block && groups[j].cl == cl) g = j;
+                if (groups[j].fn == fn && groups[j].nt == nt && groups[j].cl == cl) g = j;
             if (g < 0) {
-                groups.push_back(Group{fn, s.L.block, segs[i].op, s.L.NB, 0, {}, cl});
+                groups.push_back(Group{fn, nt, segs[i].op, s.L.NB, 0, {}, cl, auto_ws || s.L.ws});
                 g = (int)groups.size() - 1;
             }
             groups[g].smem = std::max(groups[g].smem, smem);
@@ -1053,7 +1072,7 @@ public:
                 const Slot &s0 = slots[segs[gr.seg_ids[0]].prob];
                 char key[96];
                 snprintf(key, sizeof key, "%s%dc%dt%d%s-op%d-b%d", s0.L.narrow ? "n" : "w", s0.L.Wt, s0.L.C, gr.nt,
-                         s0.L.ws ? "ws" : (s0.L.G > 1 ? "st" : "fu"), gr.op, ceil_log2(cands));
+                         gr.ws ? "ws" : (s0.L.G > 1 ? "st" : "fu"), gr.op, ceil_log2(cands));
                 tkey[g] = key;
                 c = choice[g] = tuner.pick(tkey[g], bps > 1 && !gr.cl);
             }

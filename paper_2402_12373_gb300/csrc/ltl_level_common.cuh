@@ -332,6 +332,20 @@ __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, 
     return DEC_FAIL;
 }
 
+// Sum mod 2^64 of a 64-bit value over the 32 lanes of a warp, by three
+// 32-bit warp reductions: the high words mod 2^32, and the two 16-bit halves
+// of the low words (each sum < 2^21, so exact); every lane gets the sum.
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    const uint32_t s_lo = __reduce_add_sync(0xffffffffu, lo & 0xFFFFu);
+    const uint32_t s_mid = __reduce_add_sync(0xffffffffu, lo >> 16);
+    const uint32_t s_hi = __reduce_add_sync(0xffffffffu, hi);
+    return ((uint64_t)s_hi << 32) + ((uint64_t)s_mid << 16) + (uint64_t)s_lo;
+}
+
+// Records a separator (eq. (dagger)): the first one seen wins the atomic and
+// its provenance is kept.  Callers skip the call once they know a separator
+// of the problem has been recorded (its count is only read as a flag).
 __device__ __forceinline__ void record_separator(const Problem &pb, int level, uint64_t prov) {
     if (atomicAdd(&pb.ctrl->found_count, 1u) == 0u) {
         pb.ctrl->found_prov = prov;

@@ -70,7 +70,8 @@ struct FusedShared {
     uint32_t err[32][NB];
     unsigned long long tile;
     int skip;
-    int cap_full;   // the tile's problem had a full cache when the tile was taken
+    int cap_full;     // the tile's problem had a full cache when the tile was taken
+    int found_seen;   // ... and a recorded separator
     unsigned long long idx[2][NB];
     int dec[2][NB];
     uint32_t neq[2];
@@ -209,9 +210,7 @@ __device__ __forceinline__ bool fused_tile(const Problem &pb, int level, const S
         }
         // ---- 3. CTA reduction (also frees the operand slots)
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], off);
+        for (int k = 0; k < NB; ++k) fp[k] = warp_sum_u64(fp[k]);
 #pragma unroll
         for (int k = 0; k < NB; ++k) errs[k] = __reduce_add_sync(0xffffffffu, errs[k]);
         if (lc.lane == 0) {
@@ -257,7 +256,8 @@ __device__ __forceinline__ bool fused_tile(const Problem &pb, int level, const S
             }
             if (BIN) prov = prov_pack(OP, sg.a_begin + cur_a, sg.b_begin + cur_bf + lc.lane);
             else prov = prov_pack(OP, sg.a_begin + cur_a + lc.lane, 0);
-            if (nerr <= pb.max_errors) record_separator(pb, level, prov);   // eq. (dagger), or noisy
+            // eq. (dagger), or noisy; no record once the tile's problem has one
+            if (nerr <= pb.max_errors && !sh.found_seen) record_separator(pb, level, prov);
             key = admission_key(pb, s, h);
             state = S_PROBE;
         }
@@ -417,15 +417,17 @@ __global__ void __maxnreg__((NARROW || W * C >= 8) ? 168 : 128) fused_level_kern
         // thread 0 takes a tile and reads its problem's stop flag
         if (lc.tid == 0) {
             const unsigned long long t = atomicAdd(la.tile_counter, 1ull);
-            int skip = 1, cap = 0;
+            int skip = 1, cap = 0, found = 0;
             if (t < la.total_tiles) {
                 const Ctrl *ctrl = la.probs[la.segs[find_segment(la, t)].prob].ctrl;
                 skip = ld_volatile_i32(&ctrl->stop);
                 cap = ld_volatile_i32(&ctrl->cap_hit);
+                found = ld_volatile_i32(reinterpret_cast<const int *>(&ctrl->found_count));
             }
             sh.tile = t;
             sh.skip = skip;
             sh.cap_full = cap;
+            sh.found_seen = found;
         }
         __syncthreads();
         const unsigned long long tile = sh.tile;

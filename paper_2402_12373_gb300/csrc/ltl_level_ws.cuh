@@ -173,6 +173,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
     int cur_prob = -1;
     Problem pb;
     bool alive = true;
+    unsigned long long staged = 0;   // thread 0: operand matrices copied into shared memory
     bool inflight = false;   // operand copies issued and not yet waited for
     uint64_t *ring = nullptr;
     // a timed-out wait (same outcome in every compute thread) stops the launch's work
@@ -246,6 +247,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
             const bool reload_a = BIN && (a != loaded_a);
             if (lc.tid == 0) {
                 const uint32_t n = (uint32_t)nb + (reload_a ? 1u : 0u);
+                staged += n;
                 mbar_arrive_expect_tx(&sh.ops, n * cm_bytes);
                 if (BIN) {
                     if (reload_a)
@@ -334,8 +336,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
             }
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) fp[k] += __shfl_xor_sync(0xffffffffu, fp[k], off);
+                fp[k] = warp_sum_u64(fp[k]);
                 errs[k] = __reduce_add_sync(0xffffffffu, errs[k]);
             }
             // hand the batch to the slot's hash warp
@@ -368,6 +369,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
         }
         if (!alive) break;
     }
+    if (lc.tid == 0 && staged && la.staged) atomicAdd(la.staged, staged);
     // a wait that gave up may leave this CTA's own operand copies in flight:
     // wait for them (bounded) before the CTA's shared memory goes away
     if (inflight) compute_all(lc.nt, mbar_wait_for(&sh.ops, ops_phase, 1ull << 26));
@@ -417,7 +419,7 @@ __device__ __forceinline__ int probe_round(const Problem &pb, int lane, int nb_m
 }
 
 // One matrix from a ring slot (shared memory) into its cache entry, the
-// warp's 32 lanes 16 bytes apart, 16 stores in flight per lane.
+// warp's 32 lanes 16 bytes apart.
 __device__ __forceinline__ void copy_matrix(const uint64_t *src, uint64_t *dst, uint64_t stride, int lane) {
     constexpr int kU = 8;
     for (uint64_t base = 2 * (uint64_t)lane; base < stride; base += 64 * kU) {
@@ -431,36 +433,35 @@ __device__ __forceinline__ void copy_matrix(const uint64_t *src, uint64_t *dst, 
     }
 }
 
-// Full compare of two staged matrices with two cache entries (k0 may equal k1
-// for a single one): both entries' loads are issued before any is used, so a
-// pair costs one global round trip per 16 KiB of the two.  Entries published
-// during this launch are read through L2 only (ld.cg).  Returns the bits k of
-// the candidates whose matrix differs.
-__device__ __forceinline__ uint32_t compare_two(const uint64_t *s0, const uint64_t *e0, const uint64_t *s1,
-                                                const uint64_t *e1, uint64_t stride, int lane, int k0, int k1) {
-    constexpr int kU = 8;
-    bool eq0 = true, eq1 = true;
-    for (uint64_t base = 2 * (uint64_t)lane; base < stride; base += 64 * kU) {
-        ulonglong2 q0[kU], q1[kU];
+// Full compare of a staged matrix with a cache entry, in chunks of 16
+// 16-byte pieces per lane (an 8 KiB matrix is one chunk, one global round
+// trip).  load_chunk issues a chunk's loads; differs compares the chunk
+// already in q (loaded by the caller) and then every later chunk.  Entries
+// published during this launch are read through L2 only (ld.cg).
+constexpr int kCmpUnroll = 16;
+
+__device__ __forceinline__ void load_chunk(ulonglong2 (&q)[kCmpUnroll], const uint64_t *ent, uint64_t base0,
+                                           uint64_t stride, int lane) {
+    const uint64_t base = base0 + 2 * (uint64_t)lane;
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (base + 64 * u < stride) {
-                q0[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(e0 + base + 64 * u));
-                q1[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(e1 + base + 64 * u));
-            }
+    for (int u = 0; u < kCmpUnroll; ++u)
+        if (base + 64 * u < stride) q[u] = __ldcg(reinterpret_cast<const ulonglong2 *>(ent + base + 64 * u));
+}
+
+__device__ __forceinline__ bool differs(ulonglong2 (&q)[kCmpUnroll], const uint64_t *src, const uint64_t *ent,
+                                        uint64_t stride, int lane) {
+    bool eq = true;
+    for (uint64_t base0 = 0; base0 < stride; base0 += 64 * kCmpUnroll) {
+        if (base0 > 0) load_chunk(q, ent, base0, stride, lane);
+        const uint64_t base = base0 + 2 * (uint64_t)lane;
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < kCmpUnroll; ++u)
             if (base + 64 * u < stride) {
-                const ulonglong2 v0 = *reinterpret_cast<const ulonglong2 *>(s0 + base + 64 * u);
-                const ulonglong2 v1 = *reinterpret_cast<const ulonglong2 *>(s1 + base + 64 * u);
-                eq0 &= (q0[u].x == v0.x) & (q0[u].y == v0.y);
-                eq1 &= (q1[u].x == v1.x) & (q1[u].y == v1.y);
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src + base + 64 * u);
+                eq &= (q[u].x == v.x) & (q[u].y == v.y);
             }
     }
-    uint32_t neq = 0;
-    if (__any_sync(0xffffffffu, !eq0)) neq |= 1u << k0;
-    if (__any_sync(0xffffffffu, !eq1)) neq |= 1u << k1;
-    return neq;
+    return __any_sync(0xffffffffu, !eq);
 }
 
 template <int NB, int OP>
@@ -468,6 +469,7 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                                           int lane, int ncw, unsigned long long spin_cap) {
     uint32_t uses = 0;
     int cur_prob = -1;
+    bool found_seen = false;
     Problem pb;
     unsigned long long cands_acc = 0;   // lane 0: candidates of the current problem, added on a change or at the end
     auto flush = [&]() {
@@ -497,6 +499,10 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             if (cur_prob >= 0) flush();
             cur_prob = prob;
             pb = la.probs[prob];
+            // a recorded separator of the problem makes further records unnecessary
+            found_seen = __shfl_sync(0xffffffffu,
+                                     lane == 0 ? ld_volatile_i32(reinterpret_cast<const int *>(&pb.ctrl->found_count)) : 0,
+                                     0) != 0;
         }
         const int nb = mt.nb;
         const int level = mt.level;
@@ -504,6 +510,7 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
         int state = S_DONE;
         unsigned long long key = 0, h = 0, idx = 0, waits = 0;
         uint64_t prov = 0;
+        bool sep = false;
         if (lane < nb) {
             uint64_t s = 0;
             uint32_t nerr = 0;
@@ -512,10 +519,12 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                 nerr += mt.err[w][lane];
             }
             prov = is_binary(OP) ? prov_pack(OP, mt.pa, mt.pb + (uint64_t)lane) : prov_pack(OP, mt.pa + (uint64_t)lane, 0);
-            if (nerr <= pb.max_errors) record_separator(pb, level, prov);   // eq. (dagger), or noisy
+            if (nerr <= pb.max_errors && !found_seen) record_separator(pb, level, prov);   // eq. (dagger), or noisy
             key = admission_key(pb, s, h);
             state = S_PROBE;
+            sep = nerr <= pb.max_errors;
         }
+        found_seen |= __any_sync(0xffffffffu, sep);
         // every round: probe the unsettled lanes, copy the new matrices into
         // the cache, compare the duplicates, publish, probe on after a
         // collision (a round that met another CTA's unpublished entry is
@@ -526,22 +535,27 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             const int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
             const uint32_t m_store = __ballot_sync(0xffffffffu, state == S_STORE);
             const uint32_t m_cmp = __ballot_sync(0xffffffffu, state == S_CMP);
+            // the first duplicate's loads go out before the copies, which run
+            // under their round trip
+            uint32_t neq = 0;
+            ulonglong2 q[kCmpUnroll];
+            int kc = -1;
+            if (m_cmp) {
+                kc = __ffs(m_cmp) - 1;
+                const unsigned long long ik = __shfl_sync(0xffffffffu, idx, kc);
+                load_chunk(q, pb.arena + ik * pb.stride, 0, pb.stride, lane);
+            }
             for (uint32_t m = m_store; m; m &= m - 1) {
                 const int k = __ffs(m) - 1;
                 const unsigned long long ik = __shfl_sync(0xffffffffu, idx, k);
                 copy_matrix(cms + (uint64_t)k * pb.stride, pb.arena + ik * pb.stride, pb.stride, lane);
             }
-            uint32_t neq = 0;
-            for (uint32_t m = m_cmp; m;) {
-                const int k0 = __ffs(m) - 1;
-                m &= m - 1;
-                const int k1 = m ? __ffs(m) - 1 : k0;
-                if (m) m &= m - 1;
-                const unsigned long long i0 = __shfl_sync(0xffffffffu, idx, k0);
-                const unsigned long long i1 = __shfl_sync(0xffffffffu, idx, k1);
-                neq |= compare_two(cms + (uint64_t)k0 * pb.stride, pb.arena + i0 * pb.stride,
-                                   cms + (uint64_t)k1 * pb.stride, pb.arena + i1 * pb.stride, pb.stride, lane, k0,
-                                   k1);
+            for (uint32_t m = m_cmp; m; m &= m - 1) {
+                const int k = __ffs(m) - 1;
+                const unsigned long long ik = __shfl_sync(0xffffffffu, idx, k);
+                if (k != kc) load_chunk(q, pb.arena + ik * pb.stride, 0, pb.stride, lane);
+                if (differs(q, cms + (uint64_t)k * pb.stride, pb.arena + ik * pb.stride, pb.stride, lane))
+                    neq |= 1u << k;
             }
             __syncwarp();   // every lane's share of the new matrices is written
             {

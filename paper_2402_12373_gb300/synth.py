@@ -33,6 +33,8 @@ by a separating formula):
 * ``batched``        problem i: props U{2..5}, |P|=|N| log-uniform 16..4096,
                       length U{8..64}, Bernoulli(0.3), a planted formula drawn
                       uniformly among syntax trees of size U{3..9}.
+* ``planted_large``  the plain-single shape with 1024 + 1024 traces (divide
+                      and conquer with parts the enumerator solves).
 """
 from __future__ import annotations
 
@@ -331,6 +333,15 @@ def trace_scaling(seed: int = 0, n_each: int = 32768) -> Spec:
     P = TraceSet.from_dense(np.concatenate(pos_b), np.concatenate(pos_l))
     N = TraceSet.from_dense(np.concatenate(neg_b), np.concatenate(neg_l))
     return Spec(P, N, n_props, ast_str(F_SCALE), ast_size(F_SCALE), "trace_scaling")
+
+
+def planted_large(seed: int = 0, n_each: int = 1024) -> Spec:
+    """The plain-single shape at divide-and-conquer scale: 2 props, n_each +
+    n_each traces of length U{4..10}, Bernoulli(0.5), labelled by F(p0 & X p1)
+    (size 5, U-free and in negation normal form, so every part of a split
+    has a separator within the parts' size limit)."""
+    P, N, _ = rejection_fill(seed, F_PLAIN, n_each, n_each, 2, 4, 10, 0.5)
+    return Spec(P, N, 2, ast_str(F_PLAIN), ast_size(F_PLAIN), "planted_large_%d" % n_each)
 
 
 # ---- uniform random syntax trees (for the batched workload) --------------

@@ -137,3 +137,28 @@ def test_unsolvable_and_trivial(ws):
     spec = synth.Spec(synth.TraceSet.from_list([[1], [0, 1]]), synth.TraceSet.from_list([]), 1)
     r = L.learn_dc(spec.P, spec.N, 1, max_size=3, window=2, workspace=ws)
     _check(r, spec, L.ALL, trivial=True)
+
+
+@pytest.mark.parametrize("mode", [L.DC_DETERMINISTIC, L.DC_RANDOM])
+@pytest.mark.parametrize("window", [16, 64])
+def test_planted_large_parts_are_enumerated(ws, mode, window):
+    """2048 traces labelled by F(p0 & X p1) (size 5): every part of a split
+    has a U-free NNF separator of size <= 6, so the enumerator closes parts
+    (no part needs the overfitting fallback)."""
+    spec = synth.planted_large()
+    r = L.learn_dc(spec.P, spec.N, 2, ops=NNF_NO_U, max_size=6, mode=mode, window=window, seed=2, workspace=ws)
+    _check(r, spec, NNF_NO_U)
+    assert r["enum_failed"] < r["enum_calls"]
+    assert r["fallbacks"] == 0
+
+
+@pytest.mark.parametrize("mode", [L.DC_DETERMINISTIC, L.DC_RANDOM])
+def test_single_large_parts_are_enumerated_and_combined(ws, mode):
+    """The single-large specification (2048 traces, minimal separator of size
+    8) with parts limited to size 6: no one enumeration separates it, so the
+    result combines several parts learned by enumeration."""
+    spec = synth.single_large(seed=1)
+    r = L.learn_dc(spec.P, spec.N, 3, ops=NNF_NO_U, max_size=6, mode=mode, window=64, seed=4, workspace=ws)
+    _check(r, spec, NNF_NO_U)
+    assert r["enum_calls"] >= 2
+    assert r["enum_failed"] < r["enum_calls"]
