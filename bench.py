@@ -129,7 +129,7 @@ def int_ops_per_candidate_trace(op, nsteps):
 
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for f in ("ltl_level_fused.cuh", "ltl_level_common.cuh", "ltl_device.cuh", "ltl_types.h"):
+    for f in ("ltl_level_fused.cuh", "ltl_level_ws.cuh", "ltl_level_common.cuh", "ltl_device.cuh", "ltl_types.h"):
         with open(os.path.join(ROOT, "paper_2402_12373_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -446,7 +446,7 @@ def bench_trace_scaling(L, ws, spec, steps=2):
     ach = kd_bytes / (kd_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
             "traffic": None, "kernel": "%s, every connective of size level %d" % (
-                "stream_level_kernel" if r["candidates"][kd] >= 152 else "cluster_level_kernel", kd),
+                "/".join(sorted({k for k in r["op_kernel"][kd] if k})), kd),
             "candidates": r["candidates"][kd], "level_ms": kd_ms, "algorithmic_bytes": kd_bytes,
             "peak_source": peak_src + " (hbm_gbs, copy bandwidth)"}
     return {"workload": "trace_scaling: 4 props, 32768+32768 traces, length U{33..128} (2 words per trace), "
@@ -668,8 +668,8 @@ def main():
     hbm_frac = hbm_achieved / peaks["hbm_gbs"]
     sha = kernel_sources_sha()
     traffic = profiled_traffic(sha)
-    kname = ("fused_level_kernel connective %s, size level %d (%s layout)"
-             % (OP_NAMES[od], kd, "narrow" if r0["traces_per_word"] == 2 else "wide"))
+    kname = ("%s connective %s, size level %d (%s layout)"
+             % (r0["op_kernel"][kd][od], OP_NAMES[od], kd, "narrow" if r0["traces_per_word"] == 2 else "wide"))
     hbm = {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
            "peak_source": peak_src + " (hbm_gbs, copy bandwidth)", "count": count,
            "algorithmic_bytes_per_launch": kd_bytes, "operand_matrices_staged": kd_staged,

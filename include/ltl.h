@@ -236,7 +236,14 @@ typedef struct {
                                              on the host, 0 elsewhere;
                                              a launch shared by several
                                              problems reports its total to each */
+    uint8_t op_kernel[LTL_MAX_LEVELS][8]; /* which level kernel ran each
+                                             launch ([level][op] as op_ms):
+                                             LTL_LAUNCH_*, 0 where none ran   */
 } ltl_stats;
+
+/* op_kernel values */
+enum { LTL_LAUNCH_NONE = 0, LTL_LAUNCH_FUSED = 1, LTL_LAUNCH_WS = 2, LTL_LAUNCH_STREAM = 3,
+       LTL_LAUNCH_CLUSTER = 4 };
 
 /* ---------------------------------------------------------------------------
  * ltl_learn -- learn a minimal separating formula (Section 2, the LTL learning

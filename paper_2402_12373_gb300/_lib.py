@@ -39,6 +39,9 @@ FORMULA_MAX = 512
 # level kernel used when a call does not choose one (tests switch it to run
 # every entry point on both kernels)
 DEFAULT_LEVEL_KERNEL = KERNEL_AUTO
+# ltl_stats.op_kernel values (LTL_LAUNCH_*)
+LAUNCH_KINDS = {0: None, 1: "fused_level_kernel", 2: "ws_level_kernel", 3: "stream_level_kernel",
+                4: "cluster_level_kernel"}
 # level planning used when a call does not choose one
 DEFAULT_PLANNING = PLAN_AUTO
 
@@ -81,7 +84,8 @@ class Stats(ctypes.Structure):
                 ("op_ms", (ctypes.c_float * 8) * MAX_LEVELS),
                 ("device_planned_levels", ctypes.c_uint32), ("graph_levels", ctypes.c_uint32),
                 ("compares", ctypes.c_uint64), ("collisions", ctypes.c_uint64),
-                ("op_staged", (ctypes.c_uint64 * 8) * MAX_LEVELS)]
+                ("op_staged", (ctypes.c_uint64 * 8) * MAX_LEVELS),
+                ("op_kernel", (ctypes.c_uint8 * 8) * MAX_LEVELS)]
 
     def to_dict(self, max_size: int) -> Dict:
         K = max_size
@@ -102,6 +106,7 @@ class Stats(ctypes.Structure):
             "device_planned_levels": int(self.device_planned_levels), "graph_levels": int(self.graph_levels),
             "compares": int(self.compares), "collisions": int(self.collisions),
             "op_staged": [[int(self.op_staged[c][o]) for o in range(8)] for c in range(K + 1)],
+            "op_kernel": [[LAUNCH_KINDS[int(self.op_kernel[c][o])] for o in range(8)] for c in range(K + 1)],
         }
 
 

@@ -56,6 +56,7 @@ struct Layout {
     bool ws = false;        // warp-specialised level kernel for every launch (on request)
     bool ws_ok = false;     // the warp-specialised kernel exists for this shape and its ring fits
     size_t ws_smem = 0;     // its dynamic shared memory
+    size_t stream_smem = 0; // the streaming kernel's operand ring (matrices larger than one CTA)
     uint32_t G = 0;
     uint32_t n_traces = 0, n_pos = 0;
     int n_props = 0, nsteps = 0;
@@ -227,6 +228,7 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
     L.stride = (uint64_t)L.Wt * L.plane;
     L.smem = L.G == 1 ? (size_t)(L.NB + 1) * 8 * L.stride : 0;
     if (L.CL) L.smem = (size_t)L.Wt * (L.plane / L.CL) * 8;   // the CTA's slice
+    if (L.G > 1) L.stream_smem = stream_smem_bytes(L.Wt, L.C, L.NT);
     L.block = L.NT;
     // the warp-specialised kernel adds a ring of two batches of results (its
     // own compiled batch size)
@@ -668,7 +670,8 @@ public:
         s.st.batch = (uint32_t)L.NB;
         s.st.max_entries = L.max_entries;
         int bps = 0;
-        if (occupancy(kernel_for(L, OP_U), L.block, L.CL ? 0 : L.smem, bps) == LTL_OK) s.st.ctas_per_sm = (uint32_t)bps;
+        if (occupancy(kernel_for(L, OP_U), L.block, L.G > 1 ? L.stream_smem : L.smem, bps) == LTL_OK)
+            s.st.ctas_per_sm = (uint32_t)bps;
         return LTL_OK;
     }
 
@@ -961,7 +964,10 @@ public:
             }
             // device clock from this level's planner call to the next one
             const float level_ms = lg.t_end > lg.t_begin ? (float)((double)(lg.t_end - lg.t_begin) * 1e-6) : 0.f;
-            for (int op : level_ops[i]) s.st.op_ms[k][op] = level_ms;
+            for (int op : level_ops[i]) {
+                s.st.op_ms[k][op] = level_ms;
+                s.st.op_kernel[k][op] = LTL_LAUNCH_FUSED;   // chains run the fused kernel
+            }
             s.rounds++;
             s.st.ms[k] = level_ms;
             h_ctrls[si] = lg.snap;
@@ -1011,6 +1017,7 @@ public:
             std::vector<int> seg_ids;
             int cl = 0;        // cluster size of the cluster kernel
             bool ws = false;   // the warp-specialised kernel
+            int kind = 0;      // LTL_LAUNCH_*
         };
         std::vector<Group> groups;
         // Matrices larger than one CTA: the cluster kernel (one candidate over
@@ -1035,12 +1042,19 @@ public:
                                        : kernel_for(s.L, segs[i].op);
             const int cl = cluster ? s.L.CL : 0;
             const int nt = auto_ws ? s.L.NT + kWsExtraThreads : s.L.block;
-            const size_t smem = cluster ? s.L.smem : (s.L.CL ? 0 : (auto_ws ? s.L.ws_smem : s.L.smem));
+            const size_t smem = cluster        ? s.L.smem
+                                : s.L.G > 1    ? s.L.stream_smem
+                                : auto_ws      ? s.L.ws_smem
+                                               : s.L.smem;
             int g = -1;
             for (int j = 0; j < (int)groups.size(); ++j)
                 if (groups[j].fn == fn && groups[j].nt == nt && groups[j].cl == cl) g = j;
             if (g < 0) {
-                groups.push_back(Group{fn, nt, segs[i].op, s.L.NB, 0, {}, cl, auto_ws || s.L.ws});
+                const int kind = cluster                 ? LTL_LAUNCH_CLUSTER
+                                 : (auto_ws || s.L.ws)   ? LTL_LAUNCH_WS
+                                 : s.L.G > 1             ? LTL_LAUNCH_STREAM
+                                                         : LTL_LAUNCH_FUSED;
+                groups.push_back(Group{fn, nt, segs[i].op, s.L.NB, 0, {}, cl, auto_ws || s.L.ws, kind});
                 g = (int)groups.size() - 1;
             }
             groups[g].smem = std::max(groups[g].smem, smem);
@@ -1181,6 +1195,7 @@ public:
                 for (int i : groups[g].seg_ids)
                     if (segs[i].prob == si) {
                         s.st.op_ms[k][groups[g].op] = op_ms[g];
+                        s.st.op_kernel[k][groups[g].op] = (uint8_t)groups[g].kind;
                         s.st.op_staged[k][groups[g].op] = h_staged[g];
                         break;
                     }

@@ -72,6 +72,7 @@ const void *fused_kernel_ptr_w2(int C, int op);
 const void *fused_kernel_ptr_w48(int W, int C, int op);
 const void *fused_kernel_ptr_narrow(int C, int op);
 const void *stream_kernel_ptr(int W, int C);
+size_t stream_smem_bytes(int W, int C, int NT);   // the streaming kernel's operand ring
 const void *cluster_kernel_ptr(int W, int C);
 int fused_kernel_batch(int W, int C, bool narrow);
 const void *ws_kernel_ptr_w1(int C, int op);

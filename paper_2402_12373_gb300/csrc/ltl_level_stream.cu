@@ -2,52 +2,127 @@
 // matrices larger than one CTA holds in registers (more than 4096 / W traces).
 //
 // The matrix is cut into `groups` chunk groups.  Pass 1 streams the operands
-// group by group (coalesced 16-byte loads), computing the NH fingerprint and
-// the position-0 soundness bits without keeping the matrix; after the hash
-// probe, pass 2 recomputes each group and either stores it (new entry) or
-// compares it with the stored entry of equal fingerprint.
+// group by group, computing the NH fingerprint and the position-0 soundness
+// bits without keeping the matrix; after the hash probe, pass 2 recomputes
+// each group and either stores it (new entry) or compares it with the stored
+// entry of equal fingerprint.
+//
+// The operands reach shared memory through a per-thread pipeline of
+// kStreamStages groups (cp.async, 16 bytes per copy): every thread copies
+// exactly the 16-byte pieces it will compute on, so a thread waits only for
+// its own copies and no barrier guards the ring.  The pipeline runs across
+// pass 1, the probe and pass 2 (pass 2's first groups are requested before
+// the probe), keeping several groups of loads in flight per thread where the
+// registers hold only one.
 #include "ltl_level_common.cuh"
 
 namespace ltl {
 namespace lvl {
 namespace {
 
+constexpr int kStreamStages = 3;
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gmem_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// A thread's 16-byte pieces of one group of the operands, in ring slot
+// `stage`: piece (operand o, chunk c, plane w) of thread tid at
+// ring[((stage * 2 + o) * C + c) * W + w][tid] (consecutive threads 16 bytes
+// apart, so shared-memory accesses are conflict-free).
+template <int W, int C>
+__device__ __forceinline__ ulonglong2 *ring_piece(ulonglong2 *ring, int stage, int o, int c, int w, int NT, int tid) {
+    return ring + ((((uint64_t)stage * 2 + o) * C + c) * W + w) * (uint64_t)NT + tid;
+}
+
+template <int W, int C, bool BIN>
+__device__ __forceinline__ void stage_group(const Problem &pb, const uint64_t *A, const uint64_t *B, uint32_t g,
+                                            int NT, int tid, ulonglong2 *ring, int stage) {
+    const uint64_t cs = 2ull * (uint64_t)NT;
+    const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint64_t off = (uint64_t)w * pb.plane + toff + c * cs;
+            cp_async16(ring_piece<W, C>(ring, stage, 0, c, w, NT, tid), A + off);
+            if (BIN) cp_async16(ring_piece<W, C>(ring, stage, 1, c, w, NT, tid), B + off);
+        }
+    cp_async_commit();
+}
+
+template <int W, int C, bool BIN>
+__device__ __forceinline__ void read_group(ulonglong2 *ring, int stage, int NT, int tid, Frag<W, C> &x,
+                                           Frag<W, C> &r) {
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const ulonglong2 q = *ring_piece<W, C>(ring, stage, 0, c, w, NT, tid);
+            x.v[c][0][w] = q.x;
+            x.v[c][1][w] = q.y;
+            if (BIN) {
+                const ulonglong2 q2 = *ring_piece<W, C>(ring, stage, 1, c, w, NT, tid);
+                r.v[c][0][w] = q2.x;
+                r.v[c][1][w] = q2.y;
+            }
+        }
+}
+
 struct StreamShared {
     unsigned long long fp[32];
     uint32_t err[32];
     unsigned long long tile;
     int skip;
+    int found_seen;   // the tile's problem had a recorded separator when the tile was taken
     unsigned long long idx;
     unsigned long long h;
     int dec;
 };
 
+// The connective on one group, operands already in registers (x: left or
+// only operand, r: right operand of a binary connective, the result on exit).
 template <int OP, int W, int C>
-__device__ __forceinline__ void stream_compute(const Problem &pb, const uint64_t *A, const uint64_t *B,
-                                               uint64_t toff, uint64_t cs, Frag<W, C> &r) {
-    constexpr bool BIN = is_binary(OP);
+__device__ __forceinline__ void stream_compute(const Problem &pb, uint64_t toff, uint64_t cs, Frag<W, C> &x,
+                                               Frag<W, C> &r) {
     constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
-    Frag<W, C> x, m;
-    load_frag<W, C, true>(A, pb.plane, toff, cs, x);
-    if (BIN) load_frag<W, C, true>(B, pb.plane, toff, cs, r);
+    Frag<W, C> m;
     if (MASKED) load_frag<W, C, true>(pb.mask, pb.plane, toff, cs, m);
     apply_op<OP, W, C>(r, x, m, pb.nsteps);
 }
 
 template <int W, int C, int OP>
 __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, uint64_t a, uint64_t b,
-                                                 StreamShared &sh, int NT, int tid) {
+                                                 StreamShared &sh, int NT, int tid, ulonglong2 *ring) {
     constexpr bool BIN = is_binary(OP);
     const uint64_t *A = ((OP == OP_ATOM) ? pb.atoms : pb.arena) + a * pb.stride;
     const uint64_t *B = pb.arena + b * pb.stride;
     const uint32_t G = pb.groups;
     const uint64_t cs = 2ull * (uint64_t)NT;
-    Frag<W, C> r;
+    // group sequence: pass 1 (i < G), then pass 2 (i - G); slot i % kStreamStages
+    const uint32_t total = 2 * G;
+    auto stage = [&](uint32_t i) {
+        if (i < total) stage_group<W, C, BIN>(pb, A, B, i % G, NT, tid, ring, (int)(i % kStreamStages));
+        else cp_async_commit();   // an empty group keeps the wait counts uniform
+    };
+    for (uint32_t i = 0; i < kStreamStages - 1; ++i) stage(i);
+    Frag<W, C> x, r;
     uint64_t fp = 0;
     uint32_t nerr = 0;
     for (uint32_t g = 0; g < G; ++g) {
         const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
-        stream_compute<OP, W, C>(pb, A, B, toff, cs, r);
+        cp_async_wait<kStreamStages - 2>();   // this thread's pieces of group g have landed
+        read_group<W, C, BIN>(ring, (int)(g % kStreamStages), NT, tid, x, r);
+        stage(g + kStreamStages - 1);         // the slot group g - 1 used, read before
+        stream_compute<OP, W, C>(pb, toff, cs, x, r);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             if (pb.ruc != RUC_FKP) {
@@ -69,8 +144,7 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
             }
         }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) fp += __shfl_xor_sync(0xffffffffu, fp, off);
+    fp = warp_sum_u64(fp);
     nerr = __reduce_add_sync(0xffffffffu, nerr);
     const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0) {
@@ -87,12 +161,12 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
             s += sh.fp[w2];
             total_err += sh.err[w2];
         }
-        if (total_err <= pb.max_errors) record_separator(pb, level, prov);   // eq. (dagger), or noisy
+        if (total_err <= pb.max_errors && !sh.found_seen) record_separator(pb, level, prov);   // eq. (dagger), or noisy
         unsigned long long h0 = 0;
         key = admission_key(pb, s, h0);
         sh.h = h0;
     }
-    for (;;) {
+    for (uint32_t pass2 = 0;; ++pass2) {
         if (tid == 0) {
             unsigned long long h = sh.h, idx = 0;
             // Once the cache is full nothing more is stored: the candidate has
@@ -105,13 +179,24 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
         }
         __syncthreads();
         const int d = sh.dec;
+        if (d != DEC_NEW && d != DEC_CMP) break;   // cache full (candidate still tested) or error
+        if (pass2 > 0) {   // probing on after a collision: pass 2 again, from a fresh pipeline
+            cp_async_wait_all();
+            for (uint32_t i = G; i < G + kStreamStages - 1; ++i) stage(i);
+        }
+        uint64_t *ent = pb.arena + sh.idx * pb.stride;
+        bool eq = true;
+        for (uint32_t g = 0; g < G; ++g) {
+            const uint32_t i = G + g;
+            const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
+            cp_async_wait<kStreamStages - 2>();
+            read_group<W, C, BIN>(ring, (int)(i % kStreamStages), NT, tid, x, r);
+            stage(i + kStreamStages - 1);
+            stream_compute<OP, W, C>(pb, toff, cs, x, r);
+            if (d == DEC_NEW) store_frag<W, C>(r, ent, pb.plane, toff, cs);
+            else eq &= equal_frag<W, C>(r, ent, pb.plane, toff, cs);
+        }
         if (d == DEC_NEW) {
-            uint64_t *dst = pb.arena + sh.idx * pb.stride;
-            for (uint32_t g = 0; g < G; ++g) {
-                const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
-                stream_compute<OP, W, C>(pb, A, B, toff, cs, r);
-                store_frag<W, C>(r, dst, pb.plane, toff, cs);
-            }
             __syncthreads();
             if (tid == 0) {
                 pb.prov[sh.idx] = prov;
@@ -119,43 +204,33 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
             }
             break;
         }
-        if (d == DEC_CMP) {
-            const uint64_t *src = pb.arena + sh.idx * pb.stride;
-            bool eq = true;
-            for (uint32_t g = 0; g < G; ++g) {
-                const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
-                stream_compute<OP, W, C>(pb, A, B, toff, cs, r);
-                eq &= equal_frag<W, C>(r, src, pb.plane, toff, cs);
-            }
-            const int all_eq = __syncthreads_and(eq);
-            if (tid == 0) atomicAdd(&pb.ctrl->compares, 1ull);
-            if (all_eq) break;
-            if (tid == 0) {
-                atomicAdd(&pb.ctrl->collisions, 1ull);
-                sh.h = (sh.h + 1) & pb.hmask;
-            }
-            continue;
+        const int all_eq = __syncthreads_and(eq);
+        if (tid == 0) atomicAdd(&pb.ctrl->compares, 1ull);
+        if (all_eq) break;
+        if (tid == 0) {
+            atomicAdd(&pb.ctrl->collisions, 1ull);
+            sh.h = (sh.h + 1) & pb.hmask;
         }
-        break;   // cache full (candidate still tested) or error
     }
+    cp_async_wait_all();   // no copy of this candidate is left in flight into the ring
     __syncthreads();
 }
 
 template <int W, int C, int OP>
 __device__ __forceinline__ unsigned long long stream_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0,
                                                           uint64_t a1, uint64_t b0, uint64_t b1, StreamShared &sh,
-                                                          int NT, int tid) {
+                                                          int NT, int tid, ulonglong2 *ring) {
     constexpr bool BIN = is_binary(OP);
     unsigned long long n = 0;
     for (uint64_t i = a0; i < a1; ++i) {
         if (!BIN) {
-            stream_candidate<W, C, OP>(pb, level, sg.a_begin + i, 0, sh, NT, tid);
+            stream_candidate<W, C, OP>(pb, level, sg.a_begin + i, 0, sh, NT, tid, ring);
             ++n;
             continue;
         }
         const uint64_t jb = (sg.kind == SEG_TRI) ? max(b0, i + 1) : b0;
         for (uint64_t j = jb; j < b1; ++j) {
-            stream_candidate<W, C, OP>(pb, level, sg.a_begin + i, sg.b_begin + j, sh, NT, tid);
+            stream_candidate<W, C, OP>(pb, level, sg.a_begin + i, sg.b_begin + j, sh, NT, tid, ring);
             ++n;
         }
     }
@@ -164,17 +239,33 @@ __device__ __forceinline__ unsigned long long stream_tile(const Problem &pb, int
 
 }  // namespace
 
+// Dynamic shared memory: the operand ring, kStreamStages x 2 x C x W pieces of
+// 16 bytes per thread (stream_smem_bytes).
 template <int W, int C>
 __global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
     __shared__ StreamShared sh;
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    ulonglong2 *ring = reinterpret_cast<ulonglong2 *>(dyn_smem);
     const int tid = threadIdx.x, NT = blockDim.x;
+    uint32_t dsmem;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsmem));
     for (;;) {
         if (tid == 0) {
             const unsigned long long t = atomicAdd(la.tile_counter, 1ull);
-            int skip = 1;
-            if (t < la.total_tiles) skip = ld_volatile_i32(&la.probs[la.segs[find_segment(la, t)].prob].ctrl->stop);
+            int skip = 1, found = 0;
+            if (t < la.total_tiles) {
+                const Ctrl *ctrl = la.probs[la.segs[find_segment(la, t)].prob].ctrl;
+                skip = ld_volatile_i32(&ctrl->stop);
+                found = ld_volatile_i32(reinterpret_cast<const int *>(&ctrl->found_count));
+            }
+            // the ring must fit the launch's dynamic shared memory
+            if (!skip && (uint64_t)dsmem < (uint64_t)kStreamStages * 2 * C * W * 16 * (uint64_t)NT) {
+                atomicCAS(&la.probs[la.segs[find_segment(la, t)].prob].ctrl->err, 0, -1 /* LTL_ERR_INVALID */);
+                skip = 1;
+            }
             sh.tile = t;
             sh.skip = skip;
+            sh.found_seen = found;
         }
         __syncthreads();
         const unsigned long long tile = sh.tile;
@@ -189,7 +280,7 @@ __global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
         unsigned long long done = 0;
         switch (sg.op) {
 #define LTL_STREAM_CASE(OPV) \
-    case OPV: done = stream_tile<W, C, OPV>(pb, sg.level, sg, a0, a1, b0, b1, sh, NT, tid); break;
+    case OPV: done = stream_tile<W, C, OPV>(pb, sg.level, sg, a0, a1, b0, b1, sh, NT, tid, ring); break;
             LTL_STREAM_CASE(OP_ATOM)
             LTL_STREAM_CASE(OP_NOT)
             LTL_STREAM_CASE(OP_AND)
@@ -210,6 +301,11 @@ __global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
 template <int W, int C>
 static const void *stream_fn() {
     return reinterpret_cast<const void *>(&lvl::stream_level_kernel<W, C>);
+}
+
+// Dynamic shared memory of the streaming kernel's operand ring.
+size_t stream_smem_bytes(int W, int C, int NT) {
+    return (size_t)lvl::kStreamStages * 2 * (size_t)C * (size_t)W * 16 * (size_t)NT;
 }
 
 // Streaming shapes: C * W == 8 words per thread, 128 threads per CTA.
