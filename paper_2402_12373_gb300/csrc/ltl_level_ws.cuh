@@ -12,12 +12,12 @@
 //     batch.
 //   * Two hash warps, one per ring slot, settle a staged batch completely:
 //     lane k sums the partials of candidate k, records a separator (eq.
-//     (dagger), or the noisy variant) and probes the device hash set; the warp
-//     then copies the new matrices from the ring slot into the cache (every
-//     lane a share of each matrix), compares duplicates with the stored entries
-//     (two matrices' worth of 16-byte loads in flight per lane), publishes the
-//     new entries and probes on for fingerprint collisions, before freeing the
-//     slot.
+//     (dagger), or the noisy variant) and probes the device hash set; a new
+//     matrix leaves the ring slot for the cache by one TMA bulk copy issued by
+//     its lane, the warp compares duplicates with the stored entries (a whole
+//     8 KiB matrix of 16-byte loads in flight per round trip), and the lanes
+//     publish their new entries once their copies are complete and probe on
+//     after fingerprint collisions, before the slot is freed.
 //
 // Slots hand over through two mbarriers: full (batch staged, compute -> hash)
 // and empty (slot free, hash -> compute).  Every wait is bounded; a timed-out
@@ -78,6 +78,28 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+
+// One-dimensional TMA bulk copy shared -> global (a bulk async-group of the
+// issuing thread), its commit, and the wait for its completion (the writes
+// performed), followed by the fence that orders those async-proxy writes
+// before this thread's later generic-proxy operations (the release store that
+// publishes the entry).
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_s2g_complete() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// New matrices leave a ring slot by TMA bulk copies for every connective but
+// U; U's compute threads are as busy as its hash warps, and the proxy fence
+// the bulk copies need on the compute side measured slower there.
+template <int OP>
+constexpr bool kBulkStore = OP != OP_U;
 
 // Named barrier over the compute threads only (the hash warps never join it).
 __device__ __forceinline__ void compute_sync(int nt) { asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory"); }
@@ -349,6 +371,11 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
 #pragma unroll
             for (int k = 0; k < NB; ++k)
                 if (k < cur_nb) store_frag<W, C>(r[k], dst + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs);
+            // the hash warp copies new matrices out of the slot with bulk
+            // (async-proxy) copies (every connective but U): these
+            // shared-memory writes must be visible to that proxy once the
+            // slot is handed over
+            if constexpr (kBulkStore<OP>) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             SlotMeta<NB> &mt = sh.meta[slot];
             if (lc.lane == 0) {
 #pragma unroll
@@ -533,7 +560,6 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             const bool cap_full =
                 __shfl_sync(0xffffffffu, lane == 0 ? ld_volatile_i32(&pb.ctrl->cap_hit) : 0, 0) != 0;
             const int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
-            const uint32_t m_store = __ballot_sync(0xffffffffu, state == S_STORE);
             const uint32_t m_cmp = __ballot_sync(0xffffffffu, state == S_CMP);
             // the first duplicate's loads go out before the copies, which run
             // under their round trip
@@ -545,10 +571,19 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                 const unsigned long long ik = __shfl_sync(0xffffffffu, idx, kc);
                 load_chunk(q, pb.arena + ik * pb.stride, 0, pb.stride, lane);
             }
-            for (uint32_t m = m_store; m; m &= m - 1) {
-                const int k = __ffs(m) - 1;
-                const unsigned long long ik = __shfl_sync(0xffffffffu, idx, k);
-                copy_matrix(cms + (uint64_t)k * pb.stride, pb.arena + ik * pb.stride, pb.stride, lane);
+            // each new matrix leaves the ring slot by one bulk copy issued by
+            // the candidate's own lane -- or, for U, by the warp's 16-byte
+            // stores, which keep the proxy fence off U's busier compute side
+            if constexpr (kBulkStore<OP>) {
+                if (state == S_STORE)
+                    bulk_s2g(pb.arena + idx * pb.stride, cms + (uint64_t)lane * pb.stride, (uint32_t)(pb.stride * 8));
+            } else {
+                const uint32_t m_store = __ballot_sync(0xffffffffu, state == S_STORE);
+                for (uint32_t m = m_store; m; m &= m - 1) {
+                    const int k = __ffs(m) - 1;
+                    const unsigned long long ik = __shfl_sync(0xffffffffu, idx, k);
+                    copy_matrix(cms + (uint64_t)k * pb.stride, pb.arena + ik * pb.stride, pb.stride, lane);
+                }
             }
             for (uint32_t m = m_cmp; m; m &= m - 1) {
                 const int k = __ffs(m) - 1;
@@ -557,7 +592,8 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                 if (differs(q, cms + (uint64_t)k * pb.stride, pb.arena + ik * pb.stride, pb.stride, lane))
                     neq |= 1u << k;
             }
-            __syncwarp();   // every lane's share of the new matrices is written
+            if (kBulkStore<OP> && state == S_STORE) bulk_s2g_complete();   // the new matrix is in the cache
+            __syncwarp();   // (U) every lane's share of the new matrices is written
             {
                 const uint32_t mcmp = __ballot_sync(0xffffffffu, state == S_CMP);
                 if (lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
