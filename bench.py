@@ -461,10 +461,6 @@ def bench_trace_scaling(L, ws, spec, steps=2):
                         "Bernoulli(0.25), every level until size 11 or a 120 GB cache budget",
             "status": r["status"], "levels_done": done, "unique": r["unique"][1:], "candidates": r["candidates"][1:],
             "ms": ms, "level_ms": [round(x, 3) for x in r["ms"][1:]],
-            "op_ms_last_levels": {k: {name: round(r["op_ms"][k][op], 3) for op, name in enumerate(OP_NAMES)
-                                      if r["op_ms"][k][op] > 0}
-                                  for k in range(1, len(r["ms"])) if r["ms"][k] > 0 and
-                                  k >= max(j for j in range(1, len(r["ms"])) if r["ms"][j] > 0) - 2},
             "candidates_x_traces_per_s_completed_levels": units_done / (ms / 1e3),
             "candidates_x_traces_per_s_all": units_all / (ms / 1e3),
             "launch": {"threads_per_cta": r["threads_per_cta"], "chunk_groups": r["chunk_groups"],
