@@ -7,20 +7,21 @@
 // each group and either stores it (new entry) or compares it with the stored
 // entry of equal fingerprint.
 //
-// The operands reach shared memory through a per-thread pipeline of
-// kStreamStages groups (cp.async, 16 bytes per copy): every thread copies
-// exactly the 16-byte pieces it will compute on, so a thread waits only for
-// its own copies and no barrier guards the ring.  The pipeline runs across
-// pass 1, the probe and pass 2 (pass 2's first groups are requested before
-// the probe), keeping several groups of loads in flight per thread where the
-// registers hold only one.
+// The operands -- with the length mask of Not and G and, in pass 1, the NH
+// fingerprint keys -- reach shared memory through a per-thread double-buffered
+// ring (cp.async, 16 bytes per copy): every thread copies exactly the 16-byte
+// pieces it will compute on, so a thread waits only for its own copies and no
+// barrier guards the ring.  The pipeline runs across pass 1, the probe and
+// pass 2 (pass 2's first group is requested before the probe), so the next
+// group's loads are in flight while the registers hold the current one.
 #include "ltl_level_common.cuh"
 
 namespace ltl {
 namespace lvl {
 namespace {
 
-constexpr int kStreamStages = 3;
+constexpr int kStreamStages = 2;   // ring slots (groups in flight + the one being read)
+constexpr int kStreamPieces = 3;   // per slot: left operand; right operand or length mask; NH keys
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
@@ -34,18 +35,22 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// A thread's 16-byte pieces of one group of the operands, in ring slot
-// `stage`: piece (operand o, chunk c, plane w) of thread tid at
-// ring[((stage * 2 + o) * C + c) * W + w][tid] (consecutive threads 16 bytes
-// apart, so shared-memory accesses are conflict-free).
+// A thread's 16-byte pieces of one group, in ring slot `stage`: piece
+// (kind o, chunk c, plane w) of thread tid at
+// ring[((stage * kStreamPieces + o) * C + c) * W + w][tid] (consecutive threads
+// 16 bytes apart, so shared-memory accesses are conflict-free).  Kinds: 0 the
+// left (or only) operand, 1 the right operand of a binary connective or the
+// length mask of Not and G, 2 the NH fingerprint keys (pass 1 only).
 template <int W, int C>
 __device__ __forceinline__ ulonglong2 *ring_piece(ulonglong2 *ring, int stage, int o, int c, int w, int NT, int tid) {
-    return ring + ((((uint64_t)stage * 2 + o) * C + c) * W + w) * (uint64_t)NT + tid;
+    return ring + ((((uint64_t)stage * kStreamPieces + o) * C + c) * W + w) * (uint64_t)NT + tid;
 }
 
-template <int W, int C, bool BIN>
+template <int W, int C, int OP>
 __device__ __forceinline__ void stage_group(const Problem &pb, const uint64_t *A, const uint64_t *B, uint32_t g,
-                                            int NT, int tid, ulonglong2 *ring, int stage) {
+                                            bool keys, int NT, int tid, ulonglong2 *ring, int stage) {
+    constexpr bool BIN = is_binary(OP);
+    constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
     const uint64_t cs = 2ull * (uint64_t)NT;
     const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
 #pragma unroll
@@ -55,25 +60,22 @@ __device__ __forceinline__ void stage_group(const Problem &pb, const uint64_t *A
             const uint64_t off = (uint64_t)w * pb.plane + toff + c * cs;
             cp_async16(ring_piece<W, C>(ring, stage, 0, c, w, NT, tid), A + off);
             if (BIN) cp_async16(ring_piece<W, C>(ring, stage, 1, c, w, NT, tid), B + off);
+            if (MASKED) cp_async16(ring_piece<W, C>(ring, stage, 1, c, w, NT, tid), pb.mask + off);
+            if (keys) cp_async16(ring_piece<W, C>(ring, stage, 2, c, w, NT, tid), pb.keys + off);
         }
     cp_async_commit();
 }
 
-template <int W, int C, bool BIN>
-__device__ __forceinline__ void read_group(ulonglong2 *ring, int stage, int NT, int tid, Frag<W, C> &x,
-                                           Frag<W, C> &r) {
+// Pieces of kind o into a fragment.
+template <int W, int C>
+__device__ __forceinline__ void read_piece(ulonglong2 *ring, int stage, int o, int NT, int tid, Frag<W, C> &f) {
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const ulonglong2 q = *ring_piece<W, C>(ring, stage, 0, c, w, NT, tid);
-            x.v[c][0][w] = q.x;
-            x.v[c][1][w] = q.y;
-            if (BIN) {
-                const ulonglong2 q2 = *ring_piece<W, C>(ring, stage, 1, c, w, NT, tid);
-                r.v[c][0][w] = q2.x;
-                r.v[c][1][w] = q2.y;
-            }
+            const ulonglong2 q = *ring_piece<W, C>(ring, stage, o, c, w, NT, tid);
+            f.v[c][0][w] = q.x;
+            f.v[c][1][w] = q.y;
         }
 }
 
@@ -88,14 +90,17 @@ struct StreamShared {
     int dec;
 };
 
-// The connective on one group, operands already in registers (x: left or
-// only operand, r: right operand of a binary connective, the result on exit).
+// The connective on one group, from ring slot `stage` (x: left or only
+// operand; r: the right operand of a binary connective, the result on exit).
 template <int OP, int W, int C>
-__device__ __forceinline__ void stream_compute(const Problem &pb, uint64_t toff, uint64_t cs, Frag<W, C> &x,
-                                               Frag<W, C> &r) {
+__device__ __forceinline__ void stream_compute(const Problem &pb, ulonglong2 *ring, int stage, int NT, int tid,
+                                               Frag<W, C> &x, Frag<W, C> &r) {
+    constexpr bool BIN = is_binary(OP);
     constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
     Frag<W, C> m;
-    if (MASKED) load_frag<W, C, true>(pb.mask, pb.plane, toff, cs, m);
+    read_piece<W, C>(ring, stage, 0, NT, tid, x);
+    if (BIN) read_piece<W, C>(ring, stage, 1, NT, tid, r);
+    if (MASKED) read_piece<W, C>(ring, stage, 1, NT, tid, m);
     apply_op<OP, W, C>(r, x, m, pb.nsteps);
 }
 
@@ -110,7 +115,8 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
     // group sequence: pass 1 (i < G), then pass 2 (i - G); slot i % kStreamStages
     const uint32_t total = 2 * G;
     auto stage = [&](uint32_t i) {
-        if (i < total) stage_group<W, C, BIN>(pb, A, B, i % G, NT, tid, ring, (int)(i % kStreamStages));
+        if (i < total)
+            stage_group<W, C, OP>(pb, A, B, i % G, i < G && pb.ruc != RUC_FKP, NT, tid, ring, (int)(i % kStreamStages));
         else cp_async_commit();   // an empty group keeps the wait counts uniform
     };
     for (uint32_t i = 0; i < kStreamStages - 1; ++i) stage(i);
@@ -120,16 +126,15 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
     for (uint32_t g = 0; g < G; ++g) {
         const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
         cp_async_wait<kStreamStages - 2>();   // this thread's pieces of group g have landed
-        read_group<W, C, BIN>(ring, (int)(g % kStreamStages), NT, tid, x, r);
-        stage(g + kStreamStages - 1);         // the slot group g - 1 used, read before
-        stream_compute<OP, W, C>(pb, toff, cs, x, r);
+        const int sl = (int)(g % kStreamStages);
+        stage(g + kStreamStages - 1);         // into the slot group g - 1 used, read before
+        stream_compute<OP, W, C>(pb, ring, sl, NT, tid, x, r);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             if (pb.ruc != RUC_FKP) {
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    const ulonglong2 k =
-                        __ldg(reinterpret_cast<const ulonglong2 *>(pb.keys + (uint64_t)w * pb.plane + toff + c * cs));
+                    const ulonglong2 k = *ring_piece<W, C>(ring, sl, 2, c, w, NT, tid);
                     fp += nh_term(r.v[c][0][w], k.x) + nh_term(r.v[c][1][w], k.y);
                 }
             } else {
@@ -190,9 +195,9 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
             const uint32_t i = G + g;
             const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
             cp_async_wait<kStreamStages - 2>();
-            read_group<W, C, BIN>(ring, (int)(i % kStreamStages), NT, tid, x, r);
+            const int sl = (int)(i % kStreamStages);
             stage(i + kStreamStages - 1);
-            stream_compute<OP, W, C>(pb, toff, cs, x, r);
+            stream_compute<OP, W, C>(pb, ring, sl, NT, tid, x, r);
             if (d == DEC_NEW) store_frag<W, C>(r, ent, pb.plane, toff, cs);
             else eq &= equal_frag<W, C>(r, ent, pb.plane, toff, cs);
         }
@@ -239,7 +244,7 @@ __device__ __forceinline__ unsigned long long stream_tile(const Problem &pb, int
 
 }  // namespace
 
-// Dynamic shared memory: the operand ring, kStreamStages x 2 x C x W pieces of
+// Dynamic shared memory: the ring, kStreamStages x kStreamPieces x C x W pieces of
 // 16 bytes per thread (stream_smem_bytes).
 template <int W, int C>
 __global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
                 found = ld_volatile_i32(reinterpret_cast<const int *>(&ctrl->found_count));
             }
             // the ring must fit the launch's dynamic shared memory
-            if (!skip && (uint64_t)dsmem < (uint64_t)kStreamStages * 2 * C * W * 16 * (uint64_t)NT) {
+            if (!skip && (uint64_t)dsmem < (uint64_t)kStreamStages * kStreamPieces * C * W * 16 * (uint64_t)NT) {
                 atomicCAS(&la.probs[la.segs[find_segment(la, t)].prob].ctrl->err, 0, -1 /* LTL_ERR_INVALID */);
                 skip = 1;
             }
@@ -305,7 +310,7 @@ static const void *stream_fn() {
 
 // Dynamic shared memory of the streaming kernel's operand ring.
 size_t stream_smem_bytes(int W, int C, int NT) {
-    return (size_t)lvl::kStreamStages * 2 * (size_t)C * (size_t)W * 16 * (size_t)NT;
+    return (size_t)lvl::kStreamStages * lvl::kStreamPieces * (size_t)C * (size_t)W * 16 * (size_t)NT;
 }
 
 // Streaming shapes: C * W == 8 words per thread, 128 threads per CTA.
