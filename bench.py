@@ -439,24 +439,47 @@ def bench_trace_scaling(L, ws, spec, steps=2):
     done = r["levels_done"]
     units_done = sum(r["candidates"][1:done + 1]) * T
     units_all = sum(r["candidates"][1:]) * T
-    # the largest completed size level against the HBM roof, all of its
-    # launches together (a level of fewer than 2^17 candidates runs its
-    # connectives concurrently, so only the level has a time of its own):
-    # every candidate streams its operand matrices and stores or compares one
-    # (the kernels for matrices larger than a CTA stage no operand across
-    # candidates)
-    kd = done
-    kd_ms = statistics.mean(x["ms"][kd] for _, x in runs)
+    # size levels against the HBM roof, all of a level's launches together (a
+    # level of fewer than 2^17 candidates runs its connectives concurrently,
+    # so only the level has a time of its own).  Algorithmic bytes: every
+    # candidate streams its operand matrices (the kernels for matrices larger
+    # than a CTA stage no operand across candidates); a candidate that was
+    # stored or compared adds one matrix.  In a completed level that is every
+    # candidate; in the level the cache filled during, only the candidates
+    # stored (its unique count) or compared before that (the call's compares
+    # less the duplicates of the completed levels): after it, a candidate is
+    # only tested for separation.
     cm_bytes = T * 8 * r["words_per_trace"]
-    kd_bytes = sum(op_candidates(r["unique"], kd, o, spec.n_props) * ((2 if o in (2, 3, 7) else 1) + 1)
-                   for o in range(1, 8)) * cm_bytes
     peaks, peak_src = measured_peaks()
-    ach = kd_bytes / (kd_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
-            "traffic": None, "kernel": "%s, every connective of size level %d" % (
-                "/".join(sorted({k for k in r["op_kernel"][kd] if k})), kd),
-            "candidates": r["candidates"][kd], "level_ms": kd_ms, "algorithmic_bytes": kd_bytes,
-            "peak_source": peak_src + " (hbm_gbs, copy bandwidth)"}
+
+    def level_roof(k, completed):
+        k_ms = statistics.mean(x["ms"][k] for _, x in runs)
+        operands = sum(op_candidates(r["unique"], k, o, spec.n_props) * (2 if o in (2, 3, 7) else 1)
+                       for o in range(1, 8))
+        if completed:
+            touched = r["candidates"][k]
+        else:
+            dups_before = sum(r["candidates"][i] - r["unique"][i] for i in range(1, k))
+            touched = r["unique"][k] + max(0, r["compares"] - dups_before)
+        k_bytes = (operands + touched) * cm_bytes
+        ach = k_bytes / (k_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "%s, every connective of size level %d%s" % (
+                    "/".join(sorted({x for x in r["op_kernel"][k] if x})), k,
+                    "" if completed else " (the cache filled during it)"),
+                "candidates": r["candidates"][k], "stored_or_compared": touched, "level_ms": k_ms,
+                "algorithmic_bytes": k_bytes, "peak_source": peak_src + " (hbm_gbs, copy bandwidth)"}
+
+    roof_done = level_roof(done, True) if done >= 1 else None
+    # enumerating every level (no stop at a separator), a level that has
+    # candidates but is not complete is the one the cache filled during
+    capped = done + 1 < len(r["candidates"]) and r["candidates"][done + 1] > 0
+    roof_cap = level_roof(done + 1, False) if capped else None
+    # the roofline of the leg is its longest level's
+    roof = roof_done
+    if roof_cap is not None and (roof is None or roof_cap["level_ms"] > roof["level_ms"]):
+        roof = dict(roof_cap, completed_level=roof_done)
     return {"workload": "trace_scaling: 4 props, 32768+32768 traces, length U{33..128} (2 words per trace), "
                         "Bernoulli(0.25), every level until size 11 or a 120 GB cache budget",
             "status": r["status"], "levels_done": done, "unique": r["unique"][1:], "candidates": r["candidates"][1:],

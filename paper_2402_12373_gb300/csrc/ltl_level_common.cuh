@@ -84,6 +84,56 @@ __device__ __forceinline__ void shr_any(const uint64_t (&cs)[W], uint32_t s, uin
     }
 }
 
+// Shift kinds of the log-step loops: 0 any run-time distance; 1 a run-time
+// distance below 32; K >= 32 the constant distance K.
+template <int K>
+struct ShiftKind {
+    static constexpr int value = K;
+};
+
+// A trace of W >= 2 words shifted by s < 32 positions toward position 0: as
+// 32-bit halves, every half of the result is one funnel shift of two
+// neighbouring halves.
+template <int W>
+__device__ __forceinline__ void shr_funnel(const uint64_t (&cs)[W], uint32_t s, uint64_t (&out)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint32_t lo = (uint32_t)cs[w], hi = (uint32_t)(cs[w] >> 32);
+        const uint32_t nlo = (w + 1 < W) ? (uint32_t)cs[w + 1] : 0u;
+        out[w] = ((uint64_t)__funnelshift_r(hi, nlo, s) << 32) | (uint64_t)__funnelshift_r(lo, hi, s);
+    }
+}
+
+template <int W, bool NARROW, int K>
+__device__ __forceinline__ void shr_kind(const uint64_t (&cs)[W], uint32_t s, uint64_t (&out)[W]) {
+    if constexpr (NARROW || W == 1 || K == 0) shr_any<W, NARROW>(cs, K >= 32 ? (uint32_t)K : s, out);
+    else if constexpr (K == 1) shr_funnel<W>(cs, s, out);
+    else shr<W>(cs, (uint32_t)K, out);   // a constant multiple of 32: word and half-word moves
+}
+
+// Runs step(kind, s, last) for s = 2^0 .. 2^(nsteps - 1) (last: the final
+// step).  In the wide layouts the distances below 32 run in one loop of
+// funnel shifts and the distances 32, 64, ... (one per word size, at most
+// log2(64 W) steps in all) are peeled off as constant word moves, so no
+// step needs a variable 64-bit shift with carry; narrow and one-word traces
+// keep one loop.
+template <int W, bool NARROW, class Step>
+__device__ __forceinline__ void log_steps(int nsteps, Step &&step) {
+    if constexpr (NARROW || W == 1) {
+        for (int i = 0; i < nsteps; ++i) step(ShiftKind<0>{}, 1u << i, i + 1 == nsteps);
+    } else {
+        const int ns = nsteps < 5 ? nsteps : 5;
+        for (int i = 0; i < ns; ++i) step(ShiftKind<1>{}, 1u << i, i + 1 == nsteps);
+        if (nsteps > 5) step(ShiftKind<32>{}, 32u, nsteps == 6);
+        if (nsteps > 6) step(ShiftKind<64>{}, 64u, nsteps == 7);
+        if constexpr (W >= 4)
+            if (nsteps > 7) step(ShiftKind<128>{}, 128u, nsteps == 8);
+        if constexpr (W >= 8)
+            if (nsteps > 8) step(ShiftKind<256>{}, 256u, nsteps == 9);
+        for (int i = W >= 8 ? 9 : W >= 4 ? 8 : 7; i < nsteps; ++i) step(ShiftKind<0>{}, 1u << i, i + 1 == nsteps);
+    }
+}
+
 // The connective itself (Section 4) on all of a thread's traces at once: a =
 // left operand (or the only one), r = right operand on entry for binary
 // connectives, the result on exit; m = length mask (Not and G).  The
@@ -111,18 +161,18 @@ __device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Fra
                 for (int w = 0; w < W; ++w) r.v[c][j][w] = t[w];
             }
     } else if (OP == OP_F || OP == OP_G) {
-        for (int i = 0; i < nsteps; ++i) {
-            const uint32_t s = 1u << i;
+        log_steps<W, NARROW>(nsteps, [&](auto kind, uint32_t s, bool) {
+            constexpr int K = decltype(kind)::value;
 #pragma unroll
             for (int c = 0; c < C; ++c)
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     uint64_t t[W];
-                    shr_any<W, NARROW>(r.v[c][j], s, t);
+                    shr_kind<W, NARROW, K>(r.v[c][j], s, t);
 #pragma unroll
                     for (int w = 0; w < W; ++w) r.v[c][j][w] |= t[w];
                 }
-        }
+        });
         if (OP == OP_G) {   // G f = not F not f within the trace
 #pragma unroll
             for (int c = 0; c < C; ++c)
@@ -141,24 +191,23 @@ __device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Fra
                     r.v[c][j][w] = (OP == OP_AND) ? (r.v[c][j][w] & a.v[c][j][w]) : (r.v[c][j][w] | a.v[c][j][w]);
     } else if (OP == OP_U) {
         // a: "f holds on [j, j + 2^i)"; r: "f U g within 2^i" (Lemma 2)
-        for (int i = 0; i < nsteps; ++i) {
-            const uint32_t s = 1u << i;
-            const bool last = (i + 1 == nsteps);
+        log_steps<W, NARROW>(nsteps, [&](auto kind, uint32_t s, bool last) {
+            constexpr int K = decltype(kind)::value;
 #pragma unroll
             for (int c = 0; c < C; ++c)
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     uint64_t t[W];
-                    shr_any<W, NARROW>(r.v[c][j], s, t);
+                    shr_kind<W, NARROW, K>(r.v[c][j], s, t);
 #pragma unroll
                     for (int w = 0; w < W; ++w) r.v[c][j][w] |= a.v[c][j][w] & t[w];
                     if (!last) {
-                        shr_any<W, NARROW>(a.v[c][j], s, t);
+                        shr_kind<W, NARROW, K>(a.v[c][j], s, t);
 #pragma unroll
                         for (int w = 0; w < W; ++w) a.v[c][j][w] &= t[w];
                     }
                 }
-        }
+        });
     }
 }
 
@@ -182,9 +231,8 @@ __device__ __forceinline__ void apply_binary_batch(Frag<W, C> (&r)[NB], Frag<W, 
                         r[k].v[c][j][w] =
                             (OP == OP_AND) ? (r[k].v[c][j][w] & a.v[c][j][w]) : (r[k].v[c][j][w] | a.v[c][j][w]);
     } else if (OP == OP_U) {
-        for (int i = 0; i < nsteps; ++i) {
-            const uint32_t s = 1u << i;
-            const bool last = (i + 1 == nsteps);
+        log_steps<W, NARROW>(nsteps, [&](auto kind, uint32_t s, bool last) {
+            constexpr int K = decltype(kind)::value;
 #pragma unroll
             for (int c = 0; c < C; ++c)
 #pragma unroll
@@ -192,17 +240,17 @@ __device__ __forceinline__ void apply_binary_batch(Frag<W, C> (&r)[NB], Frag<W, 
                     uint64_t t[W];
 #pragma unroll
                     for (int k = 0; k < NB; ++k) {
-                        shr_any<W, NARROW>(r[k].v[c][j], s, t);
+                        shr_kind<W, NARROW, K>(r[k].v[c][j], s, t);
 #pragma unroll
                         for (int w = 0; w < W; ++w) r[k].v[c][j][w] |= a.v[c][j][w] & t[w];
                     }
                     if (!last) {
-                        shr_any<W, NARROW>(a.v[c][j], s, t);
+                        shr_kind<W, NARROW, K>(a.v[c][j], s, t);
 #pragma unroll
                         for (int w = 0; w < W; ++w) a.v[c][j][w] &= t[w];
                     }
                 }
-        }
+        });
     }
 }
 

@@ -14,6 +14,10 @@
 // barrier guards the ring.  The pipeline runs across pass 1, the probe and
 // pass 2 (pass 2's first group is requested before the probe), so the next
 // group's loads are in flight while the registers hold the current one.
+//
+// Once the problem's cache is full, a candidate is only tested for
+// separation: nothing can be stored, so it needs no fingerprint (no keys are
+// staged and no NH term is computed), no probe and no second pass.
 #include "ltl_level_common.cuh"
 
 namespace ltl {
@@ -85,6 +89,7 @@ struct StreamShared {
     unsigned long long tile;
     int skip;
     int found_seen;   // the tile's problem had a recorded separator when the tile was taken
+    int capped;       // the problem's cache was full when the last decision was taken
     unsigned long long idx;
     unsigned long long h;
     int dec;
@@ -112,11 +117,14 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
     const uint64_t *B = pb.arena + b * pb.stride;
     const uint32_t G = pb.groups;
     const uint64_t cs = 2ull * (uint64_t)NT;
+    // a full cache (seen before this candidate) leaves only the soundness test
+    const bool capped = sh.capped != 0;
+    const bool nh = !capped && pb.ruc != RUC_FKP;
     // group sequence: pass 1 (i < G), then pass 2 (i - G); slot i % kStreamStages
-    const uint32_t total = 2 * G;
+    const uint32_t total = capped ? G : 2 * G;
     auto stage = [&](uint32_t i) {
         if (i < total)
-            stage_group<W, C, OP>(pb, A, B, i % G, i < G && pb.ruc != RUC_FKP, NT, tid, ring, (int)(i % kStreamStages));
+            stage_group<W, C, OP>(pb, A, B, i % G, i < G && nh, NT, tid, ring, (int)(i % kStreamStages));
         else cp_async_commit();   // an empty group keeps the wait counts uniform
     };
     for (uint32_t i = 0; i < kStreamStages - 1; ++i) stage(i);
@@ -131,7 +139,8 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
         stream_compute<OP, W, C>(pb, ring, sl, NT, tid, x, r);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            if (pb.ruc != RUC_FKP) {
+            if (capped) {
+            } else if (nh) {
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
                     const ulonglong2 k = *ring_piece<W, C>(ring, sl, 2, c, w, NT, tid);
@@ -178,7 +187,9 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
             // been checked for separation above, and whether it duplicates an
             // entry no longer matters, so neither the probe nor the second
             // pass (the compare) is run.
-            sh.dec = ld_volatile_i32(&pb.ctrl->cap_hit) ? (int)DEC_FAIL : probe<true>(pb, key, h, idx, false);
+            const int cap = capped || ld_volatile_i32(&pb.ctrl->cap_hit);
+            sh.capped = cap;
+            sh.dec = cap ? (int)DEC_FAIL : probe<true>(pb, key, h, idx, false);
             sh.idx = idx;
             sh.h = h;
         }
@@ -257,11 +268,12 @@ __global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
     for (;;) {
         if (tid == 0) {
             const unsigned long long t = atomicAdd(la.tile_counter, 1ull);
-            int skip = 1, found = 0;
+            int skip = 1, found = 0, cap = 0;
             if (t < la.total_tiles) {
                 const Ctrl *ctrl = la.probs[la.segs[find_segment(la, t)].prob].ctrl;
                 skip = ld_volatile_i32(&ctrl->stop);
                 found = ld_volatile_i32(reinterpret_cast<const int *>(&ctrl->found_count));
+                cap = ld_volatile_i32(&ctrl->cap_hit);
             }
             // the ring must fit the launch's dynamic shared memory
             if (!skip && (uint64_t)dsmem < (uint64_t)kStreamStages * kStreamPieces * C * W * 16 * (uint64_t)NT) {
@@ -271,6 +283,7 @@ __global__ void __launch_bounds__(256) stream_level_kernel(LevelArgs la) {
             sh.tile = t;
             sh.skip = skip;
             sh.found_seen = found;
+            sh.capped = cap;
         }
         __syncthreads();
         const unsigned long long tile = sh.tile;
