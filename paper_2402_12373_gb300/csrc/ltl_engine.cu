@@ -63,7 +63,7 @@ struct Layout {
     uint64_t plane = 0, stride = 0;
     uint64_t hslots = 0, max_entries = 0;
     size_t smem = 0;
-    size_t o_letters, o_offsets, o_mask, o_keys, o_atoms, o_hkeys, o_hvals, o_prov, o_arena, end;
+    size_t o_letters, o_offsets, o_mask, o_keys, o_atoms, o_hslots, o_prov, o_arena, end;
 };
 
 // Everything the engine needs to know about one problem's input.
@@ -262,18 +262,18 @@ ltl_status plan_layout(const ProblemIn &in, uint32_t max_chunks, uint32_t level_
     if (total <= fixed + 4096) return fail(LTL_ERR_OOM, "memory too small for the problem layout");
     const uint64_t R = total - fixed - 4096;
     const uint64_t per = 8 * L.stride + 8;   // arena + provenance per entry
-    uint64_t E = R / (per + 24);
+    const uint64_t sb = sizeof(HSlot);   // bytes per hash slot, two slots per entry
+    uint64_t E = R / (per + 2 * sb);
     uint64_t slots = pow2_ceil(std::max<uint64_t>(2 * E, 1024));
-    while (slots * 12 + E * per > R && E > 0) {
-        E = (R > slots * 12) ? (R - slots * 12) / per : 0;
+    while (slots * sb + E * per > R && E > 0) {
+        E = (R > slots * sb) ? (R - slots * sb) / per : 0;
         if (slots > 1024 && slots / 2 >= 2 * E) slots /= 2;
     }
     E = std::min<uint64_t>(E, kMaxEntries);
     if (E < 1) return fail(LTL_ERR_OOM, "memory too small for one cache entry");
     L.max_entries = E;
     L.hslots = slots;
-    L.o_hkeys = take(8 * slots);
-    L.o_hvals = take(4 * slots);
+    L.o_hslots = take(sizeof(HSlot) * slots);
     L.o_prov = take(8 * E);
     L.o_arena = take(8 * L.stride * E);
     L.end = o;
@@ -619,8 +619,7 @@ public:
         uint64_t *d_keys = (uint64_t *)(base + L.o_keys);
         uint64_t *d_atoms = (uint64_t *)(base + L.o_atoms);
         LTL_CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
-        LTL_CUDA_TRY(cudaMemsetAsync(base + L.o_hkeys, 0, 8 * L.hslots, stream));
-        LTL_CUDA_TRY(cudaMemsetAsync(base + L.o_hvals, 0xff, 4 * L.hslots, stream));
+        LTL_CUDA_TRY(cudaMemsetAsync(base + L.o_hslots, 0, sizeof(HSlot) * L.hslots, stream));
         LTL_CUDA_TRY(cudaMemsetAsync(d_mask, 0, 8 * L.stride, stream));
         LTL_CUDA_TRY(cudaMemsetAsync(d_atoms, 0, 8 * L.stride * (uint64_t)L.n_props, stream));
         if (L.narrow)
@@ -640,8 +639,7 @@ public:
         pb.keys = d_keys;
         pb.atoms = d_atoms;
         pb.prov = (uint64_t *)(base + L.o_prov);
-        pb.hkeys = (unsigned long long *)(base + L.o_hkeys);
-        pb.hvals = (uint32_t *)(base + L.o_hvals);
+        pb.hslots = (HSlot *)(base + L.o_hslots);
         pb.hmask = L.hslots - 1;
         pb.max_entries = L.max_entries;
         pb.ctrl = d_ctrl;
@@ -1376,7 +1374,7 @@ ltl_status run_single(Engine &e, ProblemIn &&in, char *formula_out, size_t formu
     Layout probe;
     ltl_status s = plan_layout(in, e.opts.max_chunks, e.opts.level_kernel, 0, (uint64_t)1 << 62, probe);
     if (s != LTL_OK) return s;
-    const size_t fixed = probe.o_hkeys + (1 << 20);
+    const size_t fixed = probe.o_hslots + (1 << 20);
     s = e.ensure_workspace(e.shared_end + fixed + (e.opts.mem_budget_bytes ? e.opts.mem_budget_bytes : 0));
     if (s != LTL_OK) return s;
     uint64_t budget = e.opts.mem_budget_bytes;

@@ -151,7 +151,7 @@ __device__ __forceinline__ void cluster_candidate(const Problem &pb, int level, 
         if (d == DEC_NEW) {
             if (leader) {
                 pb.prov[ent_idx] = prov;
-                st_release_u32(pb.hvals + h, (uint32_t)ent_idx);
+                slot_publish(pb, h, key, ent_idx);
             }
             break;
         }

@@ -42,6 +42,42 @@ __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// 128-bit compare-and-swap of a hash slot (acquire, GPU scope): if the slot
+// holds {c_key, c_val} it becomes {n_key, n_val}; the slot's previous
+// contents are returned either way.  With {0, 0} -> {0, 0} it is an atomic
+// read of the slot.
+__device__ __forceinline__ HSlot slot_cas(HSlot *p, unsigned long long c_key, unsigned long long c_val,
+                                          unsigned long long n_key, unsigned long long n_val) {
+    HSlot o;
+    asm volatile(
+        "{\n"
+        "  .reg .b128 d, b, c;\n"
+        "  mov.b128 b, {%2, %3};\n"
+        "  mov.b128 c, {%4, %5};\n"
+        "  atom.acquire.gpu.global.cas.b128 d, [%6], b, c;\n"
+        "  mov.b128 {%0, %1}, d;\n"
+        "}\n"
+        : "=l"(o.key), "=l"(o.val)
+        : "l"(c_key), "l"(c_val), "l"(n_key), "l"(n_val), "l"(p)
+        : "memory");
+    return o;
+}
+
+// Publishes a claimed slot: {key, val} by a 128-bit exchange with release
+// semantics (GPU scope), so that a reader whose slot_cas returns the index
+// also sees the entry's matrix and provenance written before.
+__device__ __forceinline__ void slot_publish(const Problem &pb, unsigned long long h, unsigned long long key,
+                                             unsigned long long val) {
+    asm volatile(
+        "{\n"
+        "  .reg .b128 d, b;\n"
+        "  mov.b128 b, {%0, %1};\n"
+        "  atom.release.gpu.global.exch.b128 d, [%2], b;\n"
+        "}\n" ::"l"(key),
+        "l"(val), "l"(pb.hslots + h)
+        : "memory");
+}
+
 template <int W, int C>
 struct Frag {
     uint64_t v[C][2][W];   // [chunk][trace of the pair][word]
@@ -334,33 +370,29 @@ template <bool kBlocking>
 __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, unsigned long long &h,
                                      unsigned long long &idx, bool full) {
     // while the cache has room (`full`: the caller's recent reading of the
-    // cache-full flag), the CAS itself reads the slot -- one round trip for an
-    // empty slot, a match or another key; a full cache stores nothing more,
-    // so then slots are only read
+    // cache-full flag), the 128-bit CAS itself reads the slot -- one round
+    // trip for an empty slot, another key, or a match whose entry index is
+    // already published; a full cache stores nothing more, so then the CAS
+    // claims nothing and only reads
     for (unsigned long long n = 0; n <= pb.hmask; ++n) {
-        unsigned long long k;
-        if (!full) {
-            k = atomicCAS(pb.hkeys + h, 0ull, key);
-            if (k == 0ull) {
-                const unsigned long long i = atomicAdd(&pb.ctrl->n_entries, 1ull);
-                if (i >= pb.max_entries) {
-                    st_release_u32(pb.hvals + h, kValFail);
-                    atomicExch(&pb.ctrl->cap_hit, 1);
-                    return DEC_FAIL;
-                }
-                idx = i;
-                return DEC_NEW;
+        HSlot *slot = pb.hslots + h;
+        HSlot o = slot_cas(slot, 0ull, 0ull, full ? 0ull : key, full ? 0ull : kValPending);
+        if (o.key == 0ull) {
+            if (full) return DEC_FAIL;
+            const unsigned long long i = atomicAdd(&pb.ctrl->n_entries, 1ull);
+            if (i >= pb.max_entries) {
+                slot_publish(pb, h, key, kValFail);
+                atomicExch(&pb.ctrl->cap_hit, 1);
+                return DEC_FAIL;
             }
-        } else {
-            k = ld_volatile_u64(pb.hkeys + h);
-            if (k == 0ull) return DEC_FAIL;
+            idx = i;
+            return DEC_NEW;
         }
-        if (k == key) {
+        if (o.key == key) {
             // relaxed admission: an equal key is a duplicate, whatever the matrix
             if (pb.ruc != RUC_EXACT) return DEC_DUP;
-            uint32_t v;
             unsigned long long spins = 0;
-            while ((v = ld_acquire_u32(pb.hvals + h)) == kValPending) {
+            while (o.val == kValPending) {
                 if (!kBlocking) return DEC_WAIT;
                 if (++spins > pb.spin_limit) {
                     atomicAdd(&pb.ctrl->timeouts, 1ull);
@@ -369,9 +401,10 @@ __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, 
                     return DEC_ERR;
                 }
                 __nanosleep(64);
+                o = slot_cas(slot, 0ull, 0ull, 0ull, 0ull);
             }
-            if (v == kValFail) return DEC_FAIL;
-            idx = v;
+            if (o.val == kValFail) return DEC_FAIL;
+            idx = o.val;
             return DEC_CMP;
         }
         h = (h + 1) & pb.hmask;

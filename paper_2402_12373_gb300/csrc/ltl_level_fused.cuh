@@ -327,7 +327,7 @@ __device__ __forceinline__ bool fused_tile(const Problem &pb, int level, const S
                 if (lc.lane == 0 && mcmp) atomicAdd(&pb.ctrl->compares, (unsigned long long)__popc(mcmp));
                 if (state == S_STORE) {
                     pb.prov[idx] = prov;
-                    st_release_u32(pb.hvals + h, (uint32_t)idx);
+                    slot_publish(pb, h, key, idx);
                     state = S_DONE;
                 } else if (state == S_CMP) {
                     if ((nq >> lc.lane) & 1u) {   // same fingerprint, different matrix

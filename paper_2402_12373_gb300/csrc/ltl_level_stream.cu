@@ -216,7 +216,7 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
             __syncthreads();
             if (tid == 0) {
                 pb.prov[sh.idx] = prov;
-                st_release_u32(pb.hvals + sh.h, (uint32_t)sh.idx);
+                slot_publish(pb, sh.h, key, sh.idx);
             }
             break;
         }

@@ -600,7 +600,7 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
             }
             if (state == S_STORE) {
                 pb.prov[idx] = prov;
-                st_release_u32(pb.hvals + h, (uint32_t)idx);
+                slot_publish(pb, h, key, idx);
                 state = S_DONE;
             } else if (state == S_CMP) {
                 if ((neq >> lane) & 1u) {   // same fingerprint, different matrix

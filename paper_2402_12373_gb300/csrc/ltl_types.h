@@ -8,8 +8,17 @@ namespace ltl {
 enum Op : int { OP_ATOM = 0, OP_NOT = 1, OP_AND = 2, OP_OR = 3, OP_X = 4, OP_F = 5, OP_G = 6, OP_U = 7 };
 
 constexpr int kMaxLevels = 64;
-constexpr uint32_t kValPending = 0xFFFFFFFFu;   // slot claimed, entry not yet published
-constexpr uint32_t kValFail = 0xFFFFFFFEu;      // slot claimed but the cache was full
+constexpr uint64_t kValPending = 0xFFFFFFFFull;   // slot claimed, entry not yet published
+constexpr uint64_t kValFail = 0xFFFFFFFEull;      // slot claimed but the cache was full
+
+// One slot of the device hash set: the fingerprint key (0 = empty) and the
+// entry index (or kValPending / kValFail), read and written together by
+// 128-bit atomics, so that the claim of a slot also returns the index an
+// earlier claimant published there.
+struct alignas(16) HSlot {
+    unsigned long long key;
+    unsigned long long val;
+};
 constexpr uint64_t kMaxEntries = (1ull << 30) - 1;
 
 // Cache admission policies (relaxed uniqueness checks, Section 5).
@@ -77,8 +86,7 @@ struct Problem {
     const uint64_t *keys;         // W planes: NH keys
     const uint64_t *atoms;        // n_props matrices (level-1 sources)
     uint64_t *prov;               // packed provenance per entry
-    unsigned long long *hkeys;    // hash slots: fingerprint (0 = empty)
-    uint32_t *hvals;              // hash slots: entry index / pending / fail
+    HSlot *hslots;                // hash slots (all zero = empty)
     uint64_t hmask;               // slots - 1
     uint64_t max_entries;
     Ctrl *ctrl;
