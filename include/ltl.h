@@ -355,8 +355,10 @@ typedef struct {
     uint64_t candidates[LTL_MAX_LEVELS];
     uint64_t n_traces;
     uint32_t rounds;              /* rounds the problem took part in           */
-    double queue_ms;              /* submission -> admission                   */
-    double latency_ms;            /* submission -> result                      */
+    double queue_ms;              /* entry of the submitting call -> admission */
+    double latency_ms;            /* entry of the submitting call -> result
+                                     (the library's copy of the traces
+                                     included)                                 */
 } ltl_result;
 
 /* Learns n problems together; out[i] is problem i's result.  opts as for

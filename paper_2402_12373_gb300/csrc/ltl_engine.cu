@@ -1330,6 +1330,8 @@ ltl_status problem_from_host(const ltl_traces *P, const ltl_traces *N, int n_pro
     if (s != LTL_OK) return s;
     if ((s = check_traces(P, "P")) != LTL_OK) return s;
     if ((s = check_traces(N, "N")) != LTL_OK) return s;
+    // a request's latency counts from here, the library's copy of its traces included
+    in.t_submit = wall_ms();
     const ltl_traces *tr[2] = {P, N};
     for (int h = 0; h < 2; ++h) {
         in.hn[h] = tr[h]->n_traces;
@@ -1353,7 +1355,6 @@ ltl_status problem_from_host(const ltl_traces *P, const ltl_traces *N, int n_pro
     in.ops = ops;
     in.max_size = max_size;
     in.budget = budget;
-    in.t_submit = wall_ms();
     return LTL_OK;
 }
 
