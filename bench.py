@@ -38,6 +38,10 @@ Metric: candidates x traces per second = sum over completed size levels of
   cpu_baseline  the oracle on the host's cores: every core (the OpenMP
            variant, identical results) and one core (the plain C oracle), on
            a bounded sample.
+  other_propagation  the same steps with the other evaluation of F, G and U
+           (by default the kernels use the carry chain; this runs the paper's
+           log-step exponential propagation), timed the same way, with its
+           counts checked equal.
 
 `--impl reference` times the oracle alone on every host core (the CPU
 reference of this workload) with the same metric.  With torchrun (N > 1)
@@ -114,16 +118,23 @@ def op_candidates(unique, k, op, n_props):
     return tot
 
 
-def int_ops_per_candidate_trace(op, nsteps):
+def int_ops_per_candidate_trace(op, nsteps, carry=True):
     """Algorithmic 32-bit integer operations per candidate and trace in the
-    narrow layout (one 32-bit word per trace), by the operators of Section 4:
-    Not, And, Or and X one operation; F a shift and an OR per log step; G the
-    same plus the masked complement before and after; U per step a shift and a
-    three-input update of the until-vector and, on every step but the last, a
-    shift and an AND of the holds-so-far vector; atoms none.  Plus 3 for the fingerprint
-    (two additions and a widening multiply-add per 64-bit word of two traces)
-    and the position-0 check."""
-    core = {0: 0, 1: 1, 2: 1, 3: 1, 4: 1, 5: 2 * nsteps, 6: 2 * nsteps + 2, 7: 4 * nsteps - 2}[op]
+    narrow layout (one 32-bit word per trace).  Not, And, Or and X: one
+    operation; atoms none.  By the carry chain (the kernels' default): F a
+    bit reversal, a negation, an OR and the reversal back; G the same between
+    two masked complements; U the reversal of both operands, an OR, an
+    addition, a three-input update and the reversal back.  By the paper's
+    exponential propagation (Section 4): F a shift and an OR per log step; G
+    the same plus the masked complements; U per step a shift and a
+    three-input update of the until-vector and, on every step but the last,
+    a shift and an AND of the holds-so-far vector.  Plus 3 for the
+    fingerprint (two additions and a widening multiply-add per 64-bit word of
+    two traces) and the position-0 check."""
+    if carry:
+        core = {0: 0, 1: 1, 2: 1, 3: 1, 4: 1, 5: 4, 6: 6, 7: 6}[op]
+    else:
+        core = {0: 0, 1: 1, 2: 1, 3: 1, 4: 1, 5: 2 * nsteps, 6: 2 * nsteps + 2, 7: 4 * nsteps - 2}[op]
     return core + 3
 
 
@@ -468,6 +479,9 @@ def bench_trace_scaling(L, ws, spec, steps=2):
                 "kernel": "%s, every connective of size level %d%s" % (
                     "/".join(sorted({x for x in r["op_kernel"][k] if x})), k,
                     "" if completed else " (the cache filled during it)"),
+                "count": "both operand matrices of every candidate, plus one per candidate stored or compared; the "
+                         "streaming kernel copies each candidate's operands from global memory and L2 serves the left "
+                         "operand that consecutive candidates share, so this fraction can exceed 1",
                 "candidates": r["candidates"][k], "stored_or_compared": touched, "level_ms": k_ms,
                 "algorithmic_bytes": k_bytes, "peak_source": peak_src + " (hbm_gbs, copy bandwidth)"}
 
@@ -573,6 +587,8 @@ def main():
                     help="launch-shape cap (16-byte chunks per thread); 0 = automatic")
     ap.add_argument("--planning", default="auto", choices=["auto", "host"],
                     help="where small size levels are planned (ltl_opts.level_planning)")
+    ap.add_argument("--propagation", default="carry", choices=["carry", "logstep"],
+                    help="F, G and U by the carry chain or by the paper's log-step exponential propagation")
     ap.add_argument("--level-kernel", default="auto", choices=["auto", "fused", "ws"],
                     help="size-level kernel: automatic choice, fused, or warp-specialised")
     ap.add_argument("--budget-gb", type=float, default=32.0,
@@ -621,6 +637,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     L.DEFAULT_LEVEL_KERNEL = {"auto": L.KERNEL_AUTO, "fused": L.KERNEL_FUSED, "ws": L.KERNEL_WS}[args.level_kernel]
     L.DEFAULT_PLANNING = {"auto": L.PLAN_AUTO, "host": L.PLAN_HOST}[args.planning]
+    L.DEFAULT_PROPAGATION = {"carry": L.PROP_CARRY, "logstep": L.PROP_LOGSTEP}[args.propagation]
     budget = min(int(args.budget_gb * 1e9), int(ws_bytes * 0.9))   # the workspace also holds the fixed parts
     ctx = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks, mem_budget=budget,
                     autotune=None if args.no_autotune else "")
@@ -712,12 +729,14 @@ def main():
     alu = None
     if r0["traces_per_word"] == 2:
         nsteps = max(1, (spec.max_len() - 1).bit_length())
-        ops_ct = int_ops_per_candidate_trace(od, nsteps)
+        carry = L.DEFAULT_PROPAGATION == L.PROP_CARRY
+        ops_ct = int_ops_per_candidate_trace(od, nsteps, carry)
         kd_ops = kd_cands * T * ops_ct
         alu_achieved = kd_ops / (kd_ms / 1e3) / 1e9
         alu = {"achieved": alu_achieved, "peak": int_peak["ops_per_s"] / 1e9, "unit": "Gop/s",
                "frac": alu_achieved / (int_peak["ops_per_s"] / 1e9), "ops_per_candidate_trace": ops_ct,
-               "log_steps": nsteps, "algorithmic_ops_per_launch": kd_ops,
+               "log_steps": nsteps, "propagation": "carry chain" if carry else "log steps",
+               "algorithmic_ops_per_launch": kd_ops,
                "peak_source": "measured on this GPU (ltl_int32_peak: chains of 32-bit shifts and three-input "
                               "logic operations, %.2f ms)" % int_peak["ms"]}
     # the roof the launch uses more of, by these algorithmic counts
@@ -762,6 +781,38 @@ def main():
         found = r
     ctx_first.close()
 
+    # the paper's evaluation of F, G and U (log-step exponential propagation,
+    # Section 4) on the same workload, timed the same way, for comparison
+    other = None
+    if rank == 0 and not args.no_extra:
+        alt = L.PROP_LOGSTEP if L.DEFAULT_PROPAGATION == L.PROP_CARRY else L.PROP_CARRY
+        ctx_alt = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks, mem_budget=budget,
+                            autotune=None if args.no_autotune else "", propagation=alt)
+        for _ in range(args.warmup):
+            ctx_alt.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
+            flush.zero_()
+        alt_times, alt_res = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ra = ctx_alt.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
+            e1.record(stream)
+            e1.synchronize()
+            alt_times.append(e0.elapsed_time(e1))
+            alt_res.append(ra)
+        ctx_alt.close()
+        other = {"propagation": "log steps (the paper's exponential propagation)" if alt == L.PROP_LOGSTEP
+                 else "carry chain",
+                 "ms_per_step": sum(alt_times) / len(alt_times),
+                 "value": sum(units_of(x, T) for x in alt_res) / (sum(alt_times) / 1e3),
+                 "dominant_launch_ms": statistics.mean(x["op_ms"][kd][od] for x in alt_res),
+                 "top_level_op_ms": {name: round(statistics.mean(x["op_ms"][K][op] for x in alt_res), 4)
+                                     for op, name in enumerate(OP_NAMES) if op > 0},
+                 "same_counts": all(x["unique"] == r0["unique"] and x["candidates"] == r0["candidates"]
+                                    for x in alt_res)}
+
     launches = sum(r["launches"] for r in results)
     if rank == 0:
         out = {
@@ -773,6 +824,7 @@ def main():
                        "mode": "enumeration-only (every level complete)",
                        "l2": "flushed between steps (512 MiB write); cache working set > L2",
                        "memory_budget_gb": budget / 1e9,
+                       "propagation": "carry chain" if L.DEFAULT_PROPAGATION == L.PROP_CARRY else "log steps",
                        "parallelism": "independent problem per rank (seed = rank)" if world > 1 else "1 GPU",
                        "launch": {"threads_per_cta": r0["threads_per_cta"],
                                   "traces_per_thread": r0["traces_per_thread"],
@@ -794,6 +846,8 @@ def main():
             "clocks": clocks,
             "autotune": autotune_summary(ctx, args.no_autotune),
         }
+        if other is not None:
+            out["other_propagation"] = other
         if extra is not None:
             out["batched"] = bench_batched(L, ws, extra[0])
             out["served"] = bench_served(L, ws, extra[1])

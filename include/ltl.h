@@ -150,6 +150,8 @@ typedef struct {
                                     matrices that fit one CTA                 */
     uint32_t level_planning;     /* LTL_PLAN_*: where the segments and tiles
                                     of a size level are planned              */
+    uint32_t propagation;        /* LTL_PROP_*: how the level kernels compute
+                                    F, G and U                               */
 } ltl_opts;
 
 /* level_kernel values.  All kernels compute the same candidates, counts and
@@ -185,6 +187,17 @@ enum { LTL_KERNEL_AUTO = 0, LTL_KERNEL_FUSED = 1, LTL_KERNEL_WS = 2 };
  *   LTL_PLAN_HOST  every level planned on the host.
  * Results, counts and formulas are the same either way. */
 enum { LTL_PLAN_AUTO = 0, LTL_PLAN_HOST = 1 };
+
+/* propagation values: two evaluations of the same operators (Section 4), so
+ * results, counts and formulas are the same either way.
+ *   LTL_PROP_CARRY    (default) the positions of each trace reversed, U's
+ *                     recursion g | (f & next) becomes the carry chain of the
+ *                     integer sum (f | g) + g, and F(x) = x | -x: a fixed
+ *                     handful of integer operations per trace word
+ *   LTL_PROP_LOGSTEP  the paper's exponential propagation: ceil(log2 Lmax)
+ *                     shift-by-2^i steps (Lemmas 1 and 2 of Appendix B)
+ * ltl_eval always uses the exponential propagation. */
+enum { LTL_PROP_CARRY = 0, LTL_PROP_LOGSTEP = 1 };
 
 #define LTL_MAX_LEVELS 64
 

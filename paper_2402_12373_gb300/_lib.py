@@ -26,6 +26,7 @@ RUC_EXACT, RUC_HASH, RUC_FKP = 0, 1, 2   # cache admission policies
 DC_DETERMINISTIC, DC_RANDOM = 0, 1       # divide-and-conquer split modes
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_WS = 0, 1, 2   # size-level kernel choice
 PLAN_AUTO, PLAN_HOST = 0, 1                       # where size levels are planned
+PROP_CARRY, PROP_LOGSTEP = 0, 1                   # how the level kernels compute F, G and U
 STOP_NONE, STOP_FIRST, STOP_LEVEL = 0, 1, 2
 MAX_LEVELS = 64
 
@@ -44,6 +45,9 @@ LAUNCH_KINDS = {0: None, 1: "fused_level_kernel", 2: "ws_level_kernel", 3: "stre
                 4: "cluster_level_kernel"}
 # level planning used when a call does not choose one
 DEFAULT_PLANNING = PLAN_AUTO
+# F/G/U evaluation used when a call does not choose one (tests switch it to
+# run the parity suite on both)
+DEFAULT_PROPAGATION = PROP_CARRY
 
 
 class LtlError(RuntimeError):
@@ -67,7 +71,8 @@ class Opts(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_uint64), ("autotune_path", ctypes.c_char_p),
                 ("max_chunks", ctypes.c_uint32), ("costs", ctypes.c_uint32 * 8),
                 ("max_errors", ctypes.c_uint32), ("ruc", ctypes.c_uint32), ("ruc_mask_bits", ctypes.c_uint32),
-                ("level_kernel", ctypes.c_uint32), ("level_planning", ctypes.c_uint32)]
+                ("level_kernel", ctypes.c_uint32), ("level_planning", ctypes.c_uint32),
+                ("propagation", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -219,7 +224,7 @@ class _HostTraces:
 def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int = 0,
           spin_limit: int = 0, max_chunks: int = 0, costs=None, max_errors: int = 0, ruc: int = RUC_EXACT,
           ruc_mask_bits: int = 0, level_kernel: Optional[int] = None, autotune: Optional[str] = None,
-          planning: Optional[int] = None) -> Opts:
+          planning: Optional[int] = None, propagation: Optional[int] = None) -> Opts:
     """costs: 8 connective costs (atoms, !, &, |, X, F, G, U), None = all 1;
     max_errors: misclassified traces a separator may have; ruc, ruc_mask_bits:
     cache admission policy and masked admission-key bits."""
@@ -246,6 +251,7 @@ def _opts(stop: int = STOP_FIRST, workspace=None, stream=None, mem_budget: int =
     o.ruc_mask_bits = int(ruc_mask_bits)
     o.level_kernel = int(DEFAULT_LEVEL_KERNEL if level_kernel is None else level_kernel)
     o.level_planning = int(DEFAULT_PLANNING if planning is None else planning)
+    o.propagation = int(DEFAULT_PROPAGATION if propagation is None else propagation)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -273,7 +279,7 @@ class Context:
                  spin_limit: int = 0, workspace_bytes: Optional[int] = None, max_chunks: int = 0,
                  costs=None, max_errors: int = 0, ruc: int = RUC_EXACT, ruc_mask_bits: int = 0,
                  level_kernel: Optional[int] = None, autotune: Optional[str] = None,
-                 planning: Optional[int] = None):
+                 planning: Optional[int] = None, propagation: Optional[int] = None):
         self._L = load()
         if workspace is None:
             workspace = default_workspace(workspace_bytes)
@@ -281,7 +287,7 @@ class Context:
         if stream is None:
             stream = _current_stream()
         self._opts = _opts(stop, workspace, stream, mem_budget, spin_limit, max_chunks, costs, max_errors, ruc,
-                           ruc_mask_bits, level_kernel, autotune, planning)
+                           ruc_mask_bits, level_kernel, autotune, planning, propagation)
         h = ctypes.c_void_p()
         _check(self._L.ltl_ctx_create(ctypes.byref(self._opts), ctypes.byref(h)), ok=(LTL_OK,))
         self._h = h

@@ -364,6 +364,8 @@ public:
         if (opts.ruc_mask_bits > 62) return fail(LTL_ERR_INVALID, "ruc_mask_bits must be at most 62");
         if (opts.level_kernel > LTL_KERNEL_WS) return fail(LTL_ERR_INVALID, "level_kernel must be LTL_KERNEL_AUTO, _FUSED or _WS");
         if (opts.level_planning > LTL_PLAN_HOST) return fail(LTL_ERR_INVALID, "level_planning must be LTL_PLAN_AUTO or _HOST");
+        if (opts.propagation > LTL_PROP_LOGSTEP)
+            return fail(LTL_ERR_INVALID, "propagation must be LTL_PROP_CARRY or LTL_PROP_LOGSTEP");
         keep_finished = keep;
         max_slots = std::max(1, std::min(max_resident, 4096));
         cudaError_t e = cudaGetDevice(&device);
@@ -646,6 +648,7 @@ public:
         pb.n_traces = (uint32_t)T;
         pb.n_pos = L.n_pos;
         pb.nsteps = L.nsteps;
+        pb.logstep = opts.propagation == LTL_PROP_LOGSTEP ? 1u : 0u;
         pb.stop_first = opts.stop_on_solution == LTL_STOP_FIRST ? 1 : 0;
         pb.groups = L.G;
         pb.max_errors = opts.max_errors;

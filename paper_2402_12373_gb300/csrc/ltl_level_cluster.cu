@@ -66,7 +66,7 @@ __device__ __forceinline__ void cluster_candidate(const Problem &pb, int level, 
         load_frag<W, C, true>(A, pb.plane, toff, cs, x);
         if (BIN) load_frag<W, C, true>(B, pb.plane, toff, cs, r);
         if (MASKED) load_frag<W, C, true>(pb.mask, pb.plane, toff, cs, m);
-        apply_op<OP, W, C>(r, x, m, pb.nsteps);
+        apply_op<OP, W, C>(r, x, m, pb.nsteps, pb.logstep != 0);
         store_frag<W, C>(r, slice, sw, toff - s0, cs);
 #pragma unroll
         for (int c = 0; c < C; ++c) {

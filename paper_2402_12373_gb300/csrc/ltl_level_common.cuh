@@ -170,13 +170,124 @@ __device__ __forceinline__ void log_steps(int nsteps, Step &&step) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Carry-chain propagation: the same F, G and U as the exponential propagation
+// of Section 4, in O(W) integer operations per trace instead of O(log n)
+// steps.  With the positions of a trace reversed (the last position least
+// significant), "at the next position" becomes "at the next less significant
+// bit", the direction in which an integer addition carries.  U's finite-trace
+// recursion r(i) = g(i) | (f(i) & r(i + 1)), r(|tr|) = 0, is then the carry
+// recursion of the sum (f | g) + g -- generate where g holds, propagate where
+// f holds -- so the carry into each bit is r at the next position and
+//     f U g = g | (f & ~((f | g) + g)).
+// F is the closure "at this position or a later one": x | -x sets every bit
+// at or above the least significant set bit.  Positions past the end of a
+// trace are zero in both operands, so no carry starts there, and the carry out
+// of position 0 is dropped.
+
+// Positions reversed: the W words of a wide trace in reverse order, each
+// bit-reversed (the last position becomes bit 0 of word 0).  A narrow word
+// holds two 32-bit traces: reversing the whole word reverses each and swaps
+// the halves, and every operation below works on the halves separately, so the
+// second reversal puts both back.
+template <int W>
+__device__ __forceinline__ void rev_trace(const uint64_t (&x)[W], uint64_t (&out)[W]) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) out[w] = __brevll(x[W - 1 - w]);
+}
+
+// a + b over a reversed trace (narrow: each 32-bit trace on its own).
+template <int W, bool NARROW>
+__device__ __forceinline__ void add_trace(const uint64_t (&a)[W], const uint64_t (&b)[W], uint64_t (&s)[W]) {
+    if constexpr (NARROW) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t lo = (uint32_t)a[w] + (uint32_t)b[w];
+            const uint32_t hi = (uint32_t)(a[w] >> 32) + (uint32_t)(b[w] >> 32);
+            s[w] = ((uint64_t)hi << 32) | (uint64_t)lo;
+        }
+    } else if constexpr (W == 1) {
+        s[0] = a[0] + b[0];
+    } else if constexpr (W == 2) {
+        asm("add.cc.u64 %0, %2, %4;\n\taddc.u64 %1, %3, %5;"
+            : "=l"(s[0]), "=l"(s[1])
+            : "l"(a[0]), "l"(a[1]), "l"(b[0]), "l"(b[1]));
+    } else if constexpr (W == 4) {
+        asm("add.cc.u64 %0, %4, %8;\n\taddc.cc.u64 %1, %5, %9;\n\taddc.cc.u64 %2, %6, %10;\n\taddc.u64 %3, %7, %11;"
+            : "=l"(s[0]), "=l"(s[1]), "=l"(s[2]), "=l"(s[3])
+            : "l"(a[0]), "l"(a[1]), "l"(a[2]), "l"(a[3]), "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]));
+    } else {
+        static_assert(W == 8, "traces of 1, 2, 4 or 8 words");
+        asm("add.cc.u64 %0, %8, %16;\n\taddc.cc.u64 %1, %9, %17;\n\taddc.cc.u64 %2, %10, %18;\n\t"
+            "addc.cc.u64 %3, %11, %19;\n\taddc.cc.u64 %4, %12, %20;\n\taddc.cc.u64 %5, %13, %21;\n\t"
+            "addc.cc.u64 %6, %14, %22;\n\taddc.u64 %7, %15, %23;"
+            : "=l"(s[0]), "=l"(s[1]), "=l"(s[2]), "=l"(s[3]), "=l"(s[4]), "=l"(s[5]), "=l"(s[6]), "=l"(s[7])
+            : "l"(a[0]), "l"(a[1]), "l"(a[2]), "l"(a[3]), "l"(a[4]), "l"(a[5]), "l"(a[6]), "l"(a[7]), "l"(b[0]),
+              "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]), "l"(b[5]), "l"(b[6]), "l"(b[7]));
+    }
+}
+
+// -a over a reversed trace (narrow: each 32-bit trace on its own).
+template <int W, bool NARROW>
+__device__ __forceinline__ void neg_trace(const uint64_t (&a)[W], uint64_t (&s)[W]) {
+    if constexpr (NARROW) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint32_t lo = 0u - (uint32_t)a[w];
+            const uint32_t hi = 0u - (uint32_t)(a[w] >> 32);
+            s[w] = ((uint64_t)hi << 32) | (uint64_t)lo;
+        }
+    } else if constexpr (W == 1) {
+        s[0] = 0ull - a[0];
+    } else if constexpr (W == 2) {
+        asm("sub.cc.u64 %0, 0, %2;\n\tsubc.u64 %1, 0, %3;" : "=l"(s[0]), "=l"(s[1]) : "l"(a[0]), "l"(a[1]));
+    } else if constexpr (W == 4) {
+        asm("sub.cc.u64 %0, 0, %4;\n\tsubc.cc.u64 %1, 0, %5;\n\tsubc.cc.u64 %2, 0, %6;\n\tsubc.u64 %3, 0, %7;"
+            : "=l"(s[0]), "=l"(s[1]), "=l"(s[2]), "=l"(s[3])
+            : "l"(a[0]), "l"(a[1]), "l"(a[2]), "l"(a[3]));
+    } else {
+        static_assert(W == 8, "traces of 1, 2, 4 or 8 words");
+        asm("sub.cc.u64 %0, 0, %8;\n\tsubc.cc.u64 %1, 0, %9;\n\tsubc.cc.u64 %2, 0, %10;\n\t"
+            "subc.cc.u64 %3, 0, %11;\n\tsubc.cc.u64 %4, 0, %12;\n\tsubc.cc.u64 %5, 0, %13;\n\t"
+            "subc.cc.u64 %6, 0, %14;\n\tsubc.u64 %7, 0, %15;"
+            : "=l"(s[0]), "=l"(s[1]), "=l"(s[2]), "=l"(s[3]), "=l"(s[4]), "=l"(s[5]), "=l"(s[6]), "=l"(s[7])
+            : "l"(a[0]), "l"(a[1]), "l"(a[2]), "l"(a[3]), "l"(a[4]), "l"(a[5]), "l"(a[6]), "l"(a[7]));
+    }
+}
+
+// F of one trace in place, by the carry chain.
+template <int W, bool NARROW>
+__device__ __forceinline__ void carry_f(uint64_t (&x)[W]) {
+    uint64_t y[W], n[W];
+    rev_trace<W>(x, y);
+    neg_trace<W, NARROW>(y, n);
+#pragma unroll
+    for (int w = 0; w < W; ++w) y[w] |= n[w];
+    rev_trace<W>(y, x);
+}
+
+// f U g of one trace into g, by the carry chain; fr = f with its positions
+// reversed (rev_trace).
+template <int W, bool NARROW>
+__device__ __forceinline__ void carry_u(const uint64_t (&fr)[W], uint64_t (&g)[W]) {
+    uint64_t gr[W], x[W], sm[W];
+    rev_trace<W>(g, gr);
+#pragma unroll
+    for (int w = 0; w < W; ++w) x[w] = fr[w] | gr[w];
+    add_trace<W, NARROW>(x, gr, sm);
+#pragma unroll
+    for (int w = 0; w < W; ++w) x[w] = gr[w] | (fr[w] & ~sm[w]);
+    rev_trace<W>(x, g);
+}
+
 // The connective itself (Section 4) on all of a thread's traces at once: a =
 // left operand (or the only one), r = right operand on entry for binary
 // connectives, the result on exit; m = length mask (Not and G).  The
 // exponential-propagation loops run step-outer, trace-inner, so each shift
 // step issues 2 * C * W independent updates.
 template <int OP, int W, int C, bool NARROW = false>
-__device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Frag<W, C> &m, int nsteps) {
+__device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Frag<W, C> &m, int nsteps,
+                                         bool logstep) {
     if (OP == OP_ATOM || OP == OP_X || OP == OP_F || OP == OP_G || OP == OP_NOT) {
 #pragma unroll
         for (int c = 0; c < C; ++c)
@@ -196,6 +307,19 @@ __device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Fra
 #pragma unroll
                 for (int w = 0; w < W; ++w) r.v[c][j][w] = t[w];
             }
+    } else if ((OP == OP_F || OP == OP_G) && !logstep) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) carry_f<W, NARROW>(r.v[c][j]);
+        if (OP == OP_G) {   // G f = not F not f within the trace
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int w = 0; w < W; ++w) r.v[c][j][w] = m.v[c][j][w] & ~r.v[c][j][w];
+        }
     } else if (OP == OP_F || OP == OP_G) {
         log_steps<W, NARROW>(nsteps, [&](auto kind, uint32_t s, bool) {
             constexpr int K = decltype(kind)::value;
@@ -225,6 +349,15 @@ __device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Fra
 #pragma unroll
                 for (int w = 0; w < W; ++w)
                     r.v[c][j][w] = (OP == OP_AND) ? (r.v[c][j][w] & a.v[c][j][w]) : (r.v[c][j][w] | a.v[c][j][w]);
+    } else if (OP == OP_U && !logstep) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                uint64_t fr[W];
+                rev_trace<W>(a.v[c][j], fr);
+                carry_u<W, NARROW>(fr, r.v[c][j]);
+            }
     } else if (OP == OP_U) {
         // a: "f holds on [j, j + 2^i)"; r: "f U g within 2^i" (Lemma 2)
         log_steps<W, NARROW>(nsteps, [&](auto kind, uint32_t s, bool last) {
@@ -254,7 +387,7 @@ __device__ __forceinline__ void apply_op(Frag<W, C> &r, Frag<W, C> &a, const Fra
 // every candidate one shift and one three-input logic operation.  Slots
 // k >= nb hold zeros and are computed like the others (uniform control flow).
 template <int OP, int W, int C, int NB, bool NARROW = false>
-__device__ __forceinline__ void apply_binary_batch(Frag<W, C> (&r)[NB], Frag<W, C> &a, int nsteps) {
+__device__ __forceinline__ void apply_binary_batch(Frag<W, C> (&r)[NB], Frag<W, C> &a, int nsteps, bool logstep) {
     if (OP == OP_AND || OP == OP_OR) {
 #pragma unroll
         for (int k = 0; k < NB; ++k)
@@ -266,6 +399,17 @@ __device__ __forceinline__ void apply_binary_batch(Frag<W, C> (&r)[NB], Frag<W, 
                     for (int w = 0; w < W; ++w)
                         r[k].v[c][j][w] =
                             (OP == OP_AND) ? (r[k].v[c][j][w] & a.v[c][j][w]) : (r[k].v[c][j][w] | a.v[c][j][w]);
+    } else if (OP == OP_U && !logstep) {
+        // the left operand is reversed once for the batch
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                uint64_t fr[W];
+                rev_trace<W>(a.v[c][j], fr);
+#pragma unroll
+                for (int k = 0; k < NB; ++k) carry_u<W, NARROW>(fr, r[k].v[c][j]);
+            }
     } else if (OP == OP_U) {
         log_steps<W, NARROW>(nsteps, [&](auto kind, uint32_t s, bool last) {
             constexpr int K = decltype(kind)::value;

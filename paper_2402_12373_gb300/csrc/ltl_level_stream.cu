@@ -106,7 +106,7 @@ __device__ __forceinline__ void stream_compute(const Problem &pb, ulonglong2 *ri
     read_piece<W, C>(ring, stage, 0, NT, tid, x);
     if (BIN) read_piece<W, C>(ring, stage, 1, NT, tid, r);
     if (MASKED) read_piece<W, C>(ring, stage, 1, NT, tid, m);
-    apply_op<OP, W, C>(r, x, m, pb.nsteps);
+    apply_op<OP, W, C>(r, x, m, pb.nsteps, pb.logstep != 0);
 }
 
 template <int W, int C, int OP>

@@ -309,7 +309,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
 #pragma unroll
                 for (int k = 0; k < NB; ++k)
                     load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
-                apply_binary_batch<OP, W, C, NB, NARROW>(r, x, pb.nsteps);
+                apply_binary_batch<OP, W, C, NB, NARROW>(r, x, pb.nsteps, pb.logstep != 0);
             }
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
@@ -322,7 +322,7 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
                                                lc.cs, x);
                         if (BIN) load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
                         if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
-                        apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps);
+                        apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps, pb.logstep != 0);
                     }
                     const uint32_t bits = pos0_bits<W, C, NARROW>(r[k]);
                     errs[k] = (uint32_t)__popc((bits ^ lc.want) & lc.care);

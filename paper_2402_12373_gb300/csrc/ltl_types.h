@@ -93,6 +93,8 @@ struct Problem {
     uint32_t n_traces;            // real traces (|P| + |N|)
     uint32_t n_pos;               // positives are traces [0, n_pos)
     int32_t nsteps;               // log-step count: ceil(log2(max length))
+    uint32_t logstep;             // F, G, U by the log-step exponential propagation
+                                  // (Section 4); 0: by the carry chain
     int32_t stop_first;           // stop at the first separator
     uint32_t groups;              // chunk groups per matrix (1: kept in registers)
     uint32_t max_errors;          // misclassified traces a separator may have

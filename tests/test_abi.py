@@ -73,7 +73,8 @@ def test_host_side_validation_without_gpu():
     import ctypes
     lib = _lib.load()
     hp = _lib._HostTraces(ts)
-    for field, bad in (("level_planning", 2), ("level_kernel", 3), ("ruc", 3), ("ruc_mask_bits", 63)):
+    for field, bad in (("level_planning", 2), ("level_kernel", 3), ("ruc", 3), ("ruc_mask_bits", 63),
+                       ("propagation", 2)):
         o = _lib._opts()
         setattr(o, field, bad)
         buf = ctypes.create_string_buffer(64)
