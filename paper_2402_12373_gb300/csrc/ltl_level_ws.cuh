@@ -311,17 +311,23 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
                     load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
                 apply_binary_batch<OP, W, C, NB, NARROW>(r, x, pb.nsteps, pb.logstep != 0);
             }
+            // the batch's shared left operand (And, Or) and the length mask
+            // (Not, G) are read once per batch
+            Frag<W, C> xs, m;
+            if constexpr (OP != OP_U && BIN) load_frag<W, C, false>(opslots + (uint64_t)NB * lc.stride, lc.plane,
+                                                                    lc.toff, lc.cs, xs);
+            if constexpr (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
                 fp[k] = 0;
                 errs[k] = 0;
                 if (k < nb) {
-                    if constexpr (OP != OP_U) {
-                        Frag<W, C> x, m;
-                        load_frag<W, C, false>(opslots + (uint64_t)(BIN ? NB : k) * lc.stride, lc.plane, lc.toff,
-                                               lc.cs, x);
-                        if (BIN) load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
-                        if (MASKED) load_frag<W, C, true>(pb.mask, lc.plane, lc.toff, lc.cs, m);
+                    if constexpr (OP != OP_U && BIN) {
+                        load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, r[k]);
+                        apply_op<OP, W, C, NARROW>(r[k], xs, m, pb.nsteps, pb.logstep != 0);
+                    } else if constexpr (OP != OP_U) {
+                        Frag<W, C> x;
+                        load_frag<W, C, false>(opslots + (uint64_t)k * lc.stride, lc.plane, lc.toff, lc.cs, x);
                         apply_op<OP, W, C, NARROW>(r[k], x, m, pb.nsteps, pb.logstep != 0);
                     }
                     const uint32_t bits = pos0_bits<W, C, NARROW>(r[k]);
