@@ -506,11 +506,14 @@ enum : int { DEC_NEW = 0, DEC_CMP = 1, DEC_FAIL = 2, DEC_ERR = 3, DEC_DUP = 4, D
 // slot's entry is not yet published, the blocking form waits (bounded); the
 // non-blocking form returns DEC_WAIT with h left on the slot, for callers that
 // may hold unpublished claims of their own (waiting there could deadlock two
-// CTAs that each wait for the other's publication).  Each lane takes its
-// entry index with its own atomicAdd: a warp-aggregated allocation (one
-// atomicAdd per warp after a ballot of the claims) measured slower, since the
-// warp's atomic waits for its slowest lane's CAS.
-template <bool kBlocking>
+// CTAs that each wait for the other's publication).  With kAlloc each lane
+// takes its entry index with its own atomicAdd (the fused, streaming and
+// cluster kernels: a warp-aggregated allocation measured slower in the fused
+// kernel, since the warp's atomic waits for its slowest lane's CAS); without
+// it a claim returns DEC_NEW and the caller allocates (claim_entry) -- the
+// warp-specialised kernel's hash warps, whose lanes' claims complete together,
+// take a round's claims with one atomic.
+template <bool kBlocking, bool kAlloc = true>
 __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, unsigned long long &h,
                                      unsigned long long &idx, bool full) {
     // while the cache has room (`full`: the caller's recent reading of the
@@ -523,6 +526,7 @@ __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, 
         HSlot o = slot_cas(slot, 0ull, 0ull, full ? 0ull : key, full ? 0ull : kValPending);
         if (o.key == 0ull) {
             if (full) return DEC_FAIL;
+            if (!kAlloc) return DEC_NEW;   // claimed; the caller allocates the entry (claim_entry)
             const unsigned long long i = atomicAdd(&pb.ctrl->n_entries, 1ull);
             if (i >= pb.max_entries) {
                 slot_publish(pb, h, key, kValFail);
@@ -555,6 +559,20 @@ __device__ __forceinline__ int probe(const Problem &pb, unsigned long long key, 
     }
     atomicExch(&pb.ctrl->cap_hit, 1);   // table full
     return DEC_FAIL;
+}
+
+// The entry of a slot claimed by probe<..., false>: index i from the
+// problem's entry counter (result DEC_NEW), or, past the cache's capacity,
+// the slot published as failed and the cache marked full (DEC_FAIL).
+__device__ __forceinline__ int claim_entry(const Problem &pb, unsigned long long h, unsigned long long key,
+                                           unsigned long long i, unsigned long long &idx) {
+    if (i >= pb.max_entries) {
+        slot_publish(pb, h, key, kValFail);
+        atomicExch(&pb.ctrl->cap_hit, 1);
+        return DEC_FAIL;
+    }
+    idx = i;
+    return DEC_NEW;
 }
 
 // Sum mod 2^64 of a 64-bit value over the 32 lanes of a warp, by three

@@ -433,7 +433,7 @@ __device__ __forceinline__ int probe_round(const Problem &pb, int lane, int nb_m
         if (k2 < lane && st2 != S_DONE && key2 == key) blocked = true;
     }
     int dec = DEC_DUP;
-    if (state == S_PROBE && !blocked) dec = probe<false>(pb, key, h, idx, cap_full);
+    if (state == S_PROBE && !blocked) dec = probe<false, false>(pb, key, h, idx, cap_full);
     if (state == S_PROBE) {
         if (blocked || dec == DEC_WAIT) {
             dec = DEC_WAIT;
@@ -565,7 +565,21 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
         while (__any_sync(0xffffffffu, state != S_DONE)) {
             const bool cap_full =
                 __shfl_sync(0xffffffffu, lane == 0 ? ld_volatile_i32(&pb.ctrl->cap_hit) : 0, 0) != 0;
-            const int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
+            int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
+            // the round's claims take consecutive entry indices with one atomic
+            // (the lanes' claims complete together, so nothing waits for a
+            // slower lane)
+            const uint32_t m_new = __ballot_sync(0xffffffffu, state == S_STORE);
+            if (m_new) {
+                const int leader = __ffs(m_new) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&pb.ctrl->n_entries, (unsigned long long)__popc(m_new));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (state == S_STORE) {
+                    dec = claim_entry(pb, h, key, base + (unsigned long long)__popc(m_new & ((1u << lane) - 1u)), idx);
+                    if (dec == DEC_FAIL) state = S_DONE;
+                }
+            }
             const uint32_t m_cmp = __ballot_sync(0xffffffffu, state == S_CMP);
             // the first duplicate's loads go out before the copies, which run
             // under their round trip
