@@ -537,6 +537,10 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
                                      lane == 0 ? ld_volatile_i32(reinterpret_cast<const int *>(&pb.ctrl->found_count)) : 0,
                                      0) != 0;
         }
+        // the cache-full flag, once per batch, read before the batch's setup so
+        // that its latency overlaps it (a stale "not full" only costs a claim
+        // that fails at allocation)
+        const int cap_raw = lane == 0 ? ld_volatile_i32(&pb.ctrl->cap_hit) : 0;
         const int nb = mt.nb;
         const int level = mt.level;
         const uint64_t *cms = opslots + (uint64_t)(NB + 1 + slot * NB) * pb.stride;
@@ -562,9 +566,8 @@ __device__ __forceinline__ void hash_role(const LevelArgs &la, WsShared<NB> &sh,
         // the cache, compare the duplicates, publish, probe on after a
         // collision (a round that met another CTA's unpublished entry is
         // retried after a short sleep)
+        const bool cap_full = __shfl_sync(0xffffffffu, cap_raw, 0) != 0;
         while (__any_sync(0xffffffffu, state != S_DONE)) {
-            const bool cap_full =
-                __shfl_sync(0xffffffffu, lane == 0 ? ld_volatile_i32(&pb.ctrl->cap_hit) : 0, 0) != 0;
             int dec = probe_round(pb, lane, NB, state, key, h, idx, waits, cap_full);
             // the round's claims take consecutive entry indices with one atomic
             // (the lanes' claims complete together, so nothing waits for a
