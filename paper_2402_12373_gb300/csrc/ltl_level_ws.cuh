@@ -206,11 +206,16 @@ __device__ __forceinline__ void compute_role(const LevelArgs &la, WsShared<NB> &
         }
         alive = false;
     };
+    // thread 0 reserves each tile one tile ahead, so that the counter's round
+    // trip overlaps the tile before
+    unsigned long long next_tile = 0;
+    if (lc.tid == 0) next_tile = atomicAdd(la.tile_counter, 1ull);
     for (;;) {
         if (lc.tid == 0) {
-            const unsigned long long t = atomicAdd(la.tile_counter, 1ull);
+            const unsigned long long t = next_tile;
             int skip = 1;
             if (t < la.total_tiles) {
+                next_tile = atomicAdd(la.tile_counter, 1ull);
                 const int si = find_segment(la, t);
                 skip = ld_volatile_i32(&la.probs[la.segs[si].prob].ctrl->stop);
             }
