@@ -26,6 +26,11 @@ namespace {
 
 constexpr int kStreamStages = 2;   // ring slots (groups in flight + the one being read)
 constexpr int kStreamPieces = 3;   // per slot: left operand; right operand or length mask; NH keys
+// Once the cache is full a candidate needs no keys: the same ring holds three
+// slots of two pieces, one more group in flight.
+constexpr int kCappedStages = 3;
+constexpr int kCappedPieces = 2;
+static_assert(kCappedStages * kCappedPieces == kStreamStages * kStreamPieces, "both rings fill the same memory");
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
@@ -45,12 +50,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 16 bytes apart, so shared-memory accesses are conflict-free).  Kinds: 0 the
 // left (or only) operand, 1 the right operand of a binary connective or the
 // length mask of Not and G, 2 the NH fingerprint keys (pass 1 only).
-template <int W, int C>
+template <int W, int C, int P = kStreamPieces>
 __device__ __forceinline__ ulonglong2 *ring_piece(ulonglong2 *ring, int stage, int o, int c, int w, int NT, int tid) {
-    return ring + ((((uint64_t)stage * kStreamPieces + o) * C + c) * W + w) * (uint64_t)NT + tid;
+    return ring + ((((uint64_t)stage * P + o) * C + c) * W + w) * (uint64_t)NT + tid;
 }
 
-template <int W, int C, int OP>
+template <int W, int C, int OP, int P = kStreamPieces>
 __device__ __forceinline__ void stage_group(const Problem &pb, const uint64_t *A, const uint64_t *B, uint32_t g,
                                             bool keys, int NT, int tid, ulonglong2 *ring, int stage) {
     constexpr bool BIN = is_binary(OP);
@@ -62,22 +67,22 @@ __device__ __forceinline__ void stage_group(const Problem &pb, const uint64_t *A
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             const uint64_t off = (uint64_t)w * pb.plane + toff + c * cs;
-            cp_async16(ring_piece<W, C>(ring, stage, 0, c, w, NT, tid), A + off);
-            if (BIN) cp_async16(ring_piece<W, C>(ring, stage, 1, c, w, NT, tid), B + off);
-            if (MASKED) cp_async16(ring_piece<W, C>(ring, stage, 1, c, w, NT, tid), pb.mask + off);
-            if (keys) cp_async16(ring_piece<W, C>(ring, stage, 2, c, w, NT, tid), pb.keys + off);
+            cp_async16(ring_piece<W, C, P>(ring, stage, 0, c, w, NT, tid), A + off);
+            if (BIN) cp_async16(ring_piece<W, C, P>(ring, stage, 1, c, w, NT, tid), B + off);
+            if (MASKED) cp_async16(ring_piece<W, C, P>(ring, stage, 1, c, w, NT, tid), pb.mask + off);
+            if (P > 2 && keys) cp_async16(ring_piece<W, C, P>(ring, stage, 2, c, w, NT, tid), pb.keys + off);
         }
     cp_async_commit();
 }
 
 // Pieces of kind o into a fragment.
-template <int W, int C>
+template <int W, int C, int P = kStreamPieces>
 __device__ __forceinline__ void read_piece(ulonglong2 *ring, int stage, int o, int NT, int tid, Frag<W, C> &f) {
 #pragma unroll
     for (int c = 0; c < C; ++c)
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-            const ulonglong2 q = *ring_piece<W, C>(ring, stage, o, c, w, NT, tid);
+            const ulonglong2 q = *ring_piece<W, C, P>(ring, stage, o, c, w, NT, tid);
             f.v[c][0][w] = q.x;
             f.v[c][1][w] = q.y;
         }
@@ -97,15 +102,15 @@ struct StreamShared {
 
 // The connective on one group, from ring slot `stage` (x: left or only
 // operand; r: the right operand of a binary connective, the result on exit).
-template <int OP, int W, int C>
+template <int OP, int W, int C, int P = kStreamPieces>
 __device__ __forceinline__ void stream_compute(const Problem &pb, ulonglong2 *ring, int stage, int NT, int tid,
                                                Frag<W, C> &x, Frag<W, C> &r) {
     constexpr bool BIN = is_binary(OP);
     constexpr bool MASKED = (OP == OP_NOT || OP == OP_G);
     Frag<W, C> m;
-    read_piece<W, C>(ring, stage, 0, NT, tid, x);
-    if (BIN) read_piece<W, C>(ring, stage, 1, NT, tid, r);
-    if (MASKED) read_piece<W, C>(ring, stage, 1, NT, tid, m);
+    read_piece<W, C, P>(ring, stage, 0, NT, tid, x);
+    if (BIN) read_piece<W, C, P>(ring, stage, 1, NT, tid, r);
+    if (MASKED) read_piece<W, C, P>(ring, stage, 1, NT, tid, m);
     apply_op<OP, W, C>(r, x, m, pb.nsteps, pb.logstep != 0);
 }
 
@@ -232,21 +237,74 @@ __device__ __forceinline__ void stream_candidate(const Problem &pb, int level, u
     __syncthreads();
 }
 
+// A candidate once the problem's cache is full: only its soundness (eq.
+// (dagger), or the noisy variant) is tested -- nothing can be stored, so it
+// needs no fingerprint, no probe and no second pass -- with one more group of
+// operands in flight than the two-pass ring holds.
+template <int W, int C, int OP>
+__device__ __forceinline__ void stream_candidate_capped(const Problem &pb, int level, uint64_t a, uint64_t b,
+                                                        StreamShared &sh, int NT, int tid, ulonglong2 *ring) {
+    constexpr bool BIN = is_binary(OP);
+    constexpr int ST = kCappedStages, P = kCappedPieces;
+    const uint64_t *A = ((OP == OP_ATOM) ? pb.atoms : pb.arena) + a * pb.stride;
+    const uint64_t *B = pb.arena + b * pb.stride;
+    const uint32_t G = pb.groups;
+    const uint64_t cs = 2ull * (uint64_t)NT;
+    auto stage = [&](uint32_t i) {
+        if (i < G) stage_group<W, C, OP, P>(pb, A, B, i, false, NT, tid, ring, (int)(i % ST));
+        else cp_async_commit();   // an empty group keeps the wait counts uniform
+    };
+    for (uint32_t i = 0; i < ST - 1; ++i) stage(i);
+    Frag<W, C> x, r;
+    uint32_t nerr = 0;
+    for (uint32_t g = 0; g < G; ++g) {
+        const uint64_t toff = 2ull * ((uint64_t)g * C * NT + (uint64_t)tid);
+        cp_async_wait<ST - 2>();   // this thread's pieces of group g have landed
+        const int sl = (int)(g % ST);
+        stage(g + ST - 1);         // into the slot group g - 1 used, read before
+        stream_compute<OP, W, C, P>(pb, ring, sl, NT, tid, x, r);
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const uint64_t t = toff + c * cs + (uint64_t)j;
+                const bool v = (r.v[c][j][0] & 1ull) != 0;
+                nerr += ((t < pb.n_traces) && (v != (t < pb.n_pos))) ? 1u : 0u;
+            }
+    }
+    nerr = __reduce_add_sync(0xffffffffu, nerr);
+    if ((tid & 31) == 0) sh.err[tid >> 5] = nerr;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t total_err = 0;
+        for (int w2 = 0; w2 < (NT >> 5); ++w2) total_err += sh.err[w2];
+        if (total_err <= pb.max_errors && !sh.found_seen) record_separator(pb, level, prov_pack(OP, a, BIN ? b : 0));
+    }
+    cp_async_wait_all();   // no copy of this candidate is left in flight into the ring
+    __syncthreads();
+}
+
 template <int W, int C, int OP>
 __device__ __forceinline__ unsigned long long stream_tile(const Problem &pb, int level, const Seg &sg, uint64_t a0,
                                                           uint64_t a1, uint64_t b0, uint64_t b1, StreamShared &sh,
                                                           int NT, int tid, ulonglong2 *ring) {
     constexpr bool BIN = is_binary(OP);
     unsigned long long n = 0;
+    // sh.capped is read after the barrier that ends the previous candidate (or
+    // the tile fetch), so every thread takes the same path
+    auto one = [&](uint64_t a, uint64_t b) {
+        if (sh.capped) stream_candidate_capped<W, C, OP>(pb, level, a, b, sh, NT, tid, ring);
+        else stream_candidate<W, C, OP>(pb, level, a, b, sh, NT, tid, ring);
+    };
     for (uint64_t i = a0; i < a1; ++i) {
         if (!BIN) {
-            stream_candidate<W, C, OP>(pb, level, sg.a_begin + i, 0, sh, NT, tid, ring);
+            one(sg.a_begin + i, 0);
             ++n;
             continue;
         }
         const uint64_t jb = (sg.kind == SEG_TRI) ? max(b0, i + 1) : b0;
         for (uint64_t j = jb; j < b1; ++j) {
-            stream_candidate<W, C, OP>(pb, level, sg.a_begin + i, sg.b_begin + j, sh, NT, tid, ring);
+            one(sg.a_begin + i, sg.b_begin + j);
             ++n;
         }
     }

@@ -237,6 +237,29 @@ def test_cap_reached_with_small_budget(ws):
     assert got["unique"][1:d + 1] == want["unique"][1:d + 1]
 
 
+def test_streaming_cache_fills_during_a_level(ws):
+    """Matrices larger than a CTA (the two-pass streaming kernel) with a cache
+    that fills during a level: the candidates after that are only tested for
+    separation (no fingerprint, probe or second pass).  Completed levels,
+    the capped level's candidate count, the status and a found size equal the
+    oracle's with the same capacity."""
+    s = synth.single_large(n_each=3000)
+    with L.Context(workspace=ws, stop=L.STOP_NONE, mem_budget=64 << 20, level_kernel=L.KERNEL_FUSED) as ctx:
+        got = ctx.learn(s.P, s.N, 3, max_size=8)
+    assert got["chunk_groups"] > 1
+    assert got["status"] in ("cap", "found")
+    d = got["levels_done"]
+    assert got["candidates"][d + 1] > 0 and got["entries"] == got["max_entries"]   # filled during level d + 1
+    want = O.learn(s.P, s.N, 3, max_size=8, stop_mode=0, max_entries=got["max_entries"])
+    assert want["levels_done"] == d
+    assert got["status"] == want["status"]
+    assert got["unique"][1:d + 1] == want["unique"][1:d + 1]
+    assert got["candidates"][1:d + 2] == want["candidates"][1:d + 2]
+    if got["status"] == "found":
+        assert got["size"] == want["size"]
+        assert O.separates(got["formula"], s.P, s.N, 3)
+
+
 def _long_traces(seed, n_each, lo, hi, n_props=2):
     rng = random.Random(seed)
     mk = lambda: [rng.randrange(1 << n_props) for _ in range(rng.randrange(lo, hi + 1))]
