@@ -154,6 +154,29 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def stream_sources_sha():
+    h = hashlib.sha256()
+    for f in ("ltl_level_stream.cu", "ltl_level_common.cuh", "ltl_device.cuh", "ltl_types.h"):
+        with open(os.path.join(ROOT, "paper_2402_12373_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stream_traffic_per_candidate():
+    """Physical DRAM bytes per candidate of the streaming kernel from a
+    committed ncu summary of a small trace-scaling case whose cache fills
+    during the captured level, if it was taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "stream_kernel_trace_scaling.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("stream_sources_sha") == stream_sources_sha():
+            return d.get("dram_bytes_per_candidate")
+    except Exception:
+        pass
+    return None
+
+
 def profiled_traffic(sha):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
     summary, if it was taken on the current kernel sources."""
@@ -491,6 +514,17 @@ def bench_trace_scaling(L, ws, spec, steps=2):
     capped = done + 1 < len(r["candidates"]) and r["candidates"][done + 1] > 0
     roof_cap = level_roof(done + 1, False) if capped else None
     # the roofline of the leg is its longest level's
+    if roof_cap is not None:
+        # physical DRAM bytes: an ncu capture of a small case scaled by candidates
+        per_cand = stream_traffic_per_candidate()
+        if per_cand:
+            traffic = per_cand * roof_cap["candidates"]
+            roof_cap["traffic"] = traffic
+            roof_cap["dram"] = {"bytes": traffic, "gbs": traffic / (roof_cap["level_ms"] / 1e3) / 1e9,
+                                "frac": traffic / (roof_cap["level_ms"] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                "source": "ncu DRAM bytes per candidate of a size-5 trace-scaling launch whose cache "
+                                          "fills during it (profiles/stream_kernel_trace_scaling.json), times this "
+                                          "level's candidates"}
     roof = roof_done
     if roof_cap is not None and (roof is None or roof_cap["level_ms"] > roof["level_ms"]):
         roof = dict(roof_cap, completed_level=roof_done)
