@@ -784,6 +784,13 @@ def main():
         # physical DRAM bytes of the launch (ncu, same kernel sources) over its event time
         roofline["dram"] = {"bytes_per_launch": traffic, "gbs": traffic / (kd_ms / 1e3) / 1e9,
                             "frac": traffic / (kd_ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+        if alu is not None and max(roofline["dram"]["frac"], alu["frac"]) < 0.5:
+            # neither physical roof is near: say what the launch waits on
+            roofline["limiter"] = ("latency: physical DRAM traffic at %.2f of the copy bandwidth and integer work at "
+                                   "%.2f of the measured integer roof; the hash warps' global round trips (claim, "
+                                   "allocation or compare, publication) and the compute warps' dependent chains "
+                                   "(ncu: long-scoreboard and wait stalls lead, profiles/level_kernel_single_large.md)"
+                                   % (roofline["dram"]["frac"], alu["frac"]))
     kernel_ms = [sum(r["ms"][k] for k in range(1, r["levels_done"] + 1)) for r in results]
 
     # end to end: host trace buffers through ltl_ctx_learn (one untimed call
