@@ -319,6 +319,14 @@ public:
     WalkJob *h_jobs = nullptr;
     uint32_t *h_tokens = nullptr;
     int *h_ntok = nullptr;
+    // Pinned staging of small host inputs: a problem's letters and offsets are
+    // copied into this buffer and uploaded from it asynchronously (from
+    // pageable memory each upload would wait for the stream); the buffer is
+    // reused once the stream has drained.
+    static constexpr size_t kPinStageMax = (size_t)4 << 20;     // inputs staged when at most this size
+    static constexpr size_t kPinStageBytes = (size_t)64 << 20;
+    char *h_pin = nullptr;
+    size_t pin_head = 0;
     std::vector<Slot> slots;
     FreeList mem;
     struct Occ {
@@ -438,6 +446,8 @@ public:
         if (h_ntok) cudaFreeHost(h_ntok);
         if (h_plan_state) cudaFreeHost(h_plan_state);
         if (h_plan_log) cudaFreeHost(h_plan_log);
+        if (h_pin) cudaFreeHost(h_pin);
+        h_pin = nullptr;
         h_probs = nullptr; h_ctrls = nullptr; h_staged = nullptr; h_segs = nullptr; h_jobs = nullptr; h_tokens = nullptr; h_ntok = nullptr;
         h_plan_state = nullptr; h_plan_log = nullptr;
         if (ev_begin) cudaEventDestroy(ev_begin);
@@ -606,14 +616,33 @@ public:
             uint32_t *dl = (uint32_t *)(base + L.o_letters);
             uint64_t *dof = (uint64_t *)(base + L.o_offsets);
             const uint64_t np = s.in.ho[0][s.in.hn[0]], nn = s.in.ho[1][s.in.hn[1]];
-            std::vector<uint64_t> offv(T + 1);
-            for (uint64_t i = 0; i <= s.in.hn[0]; ++i) offv[i] = s.in.ho[0][i];
-            for (uint64_t i = 1; i <= s.in.hn[1]; ++i) offv[s.in.hn[0] + i] = np + s.in.ho[1][i];
-            if (np) LTL_CUDA_TRY(cudaMemcpyAsync(dl, s.in.hl[0], 4 * np, cudaMemcpyHostToDevice, stream));
-            if (nn) LTL_CUDA_TRY(cudaMemcpyAsync(dl + np, s.in.hl[1], 4 * nn, cudaMemcpyHostToDevice, stream));
-            LTL_CUDA_TRY(cudaMemcpyAsync(dof, offv.data(), 8 * (T + 1), cudaMemcpyHostToDevice, stream));
+            const size_t lb = round_up(4 * (np + nn), 256), need = lb + round_up(8 * (T + 1), 256);
+            if (need <= kPinStageMax) {
+                if (!h_pin || pin_head + need > kPinStageBytes) {
+                    // every earlier staged upload has landed before the buffer is reused
+                    LTL_CUDA_TRY(cudaStreamSynchronize(stream));
+                    pin_head = 0;
+                    if (!h_pin) LTL_CUDA_TRY(cudaMallocHost(&h_pin, kPinStageBytes));
+                }
+                uint32_t *pl = (uint32_t *)(h_pin + pin_head);
+                uint64_t *po = (uint64_t *)(h_pin + pin_head + lb);
+                if (np) memcpy(pl, s.in.hl[0], 4 * np);
+                if (nn) memcpy(pl + np, s.in.hl[1], 4 * nn);
+                for (uint64_t i = 0; i <= s.in.hn[0]; ++i) po[i] = s.in.ho[0][i];
+                for (uint64_t i = 1; i <= s.in.hn[1]; ++i) po[s.in.hn[0] + i] = np + s.in.ho[1][i];
+                if (np + nn) LTL_CUDA_TRY(cudaMemcpyAsync(dl, pl, 4 * (np + nn), cudaMemcpyHostToDevice, stream));
+                LTL_CUDA_TRY(cudaMemcpyAsync(dof, po, 8 * (T + 1), cudaMemcpyHostToDevice, stream));
+                pin_head += need;
+            } else {
+                std::vector<uint64_t> offv(T + 1);
+                for (uint64_t i = 0; i <= s.in.hn[0]; ++i) offv[i] = s.in.ho[0][i];
+                for (uint64_t i = 1; i <= s.in.hn[1]; ++i) offv[s.in.hn[0] + i] = np + s.in.ho[1][i];
+                if (np) LTL_CUDA_TRY(cudaMemcpyAsync(dl, s.in.hl[0], 4 * np, cudaMemcpyHostToDevice, stream));
+                if (nn) LTL_CUDA_TRY(cudaMemcpyAsync(dl + np, s.in.hl[1], 4 * nn, cudaMemcpyHostToDevice, stream));
+                LTL_CUDA_TRY(cudaMemcpyAsync(dof, offv.data(), 8 * (T + 1), cudaMemcpyHostToDevice, stream));
+                LTL_CUDA_TRY(cudaStreamSynchronize(stream));   // offv is pageable and local
+            }
             s.st.h2d_bytes += 4 * (np + nn) + 8 * (T + 1);
-            LTL_CUDA_TRY(cudaStreamSynchronize(stream));   // offv is pageable and local
             d_letters = dl;
             d_offsets = dof;
         }
