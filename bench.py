@@ -284,9 +284,11 @@ def autotune_summary(ctx, off):
 
 def _oracle_rate(learn, spec, max_size, target_s):
     """candidates x traces per second of one oracle entry point, sizes
-    1..max_size of `spec` enumerated completely, repeated for ~target_s."""
+    1..max_size of `spec` enumerated completely, repeated for ~target_s; and
+    the oracle's own time per size level, averaged over the runs (ms)."""
     T = spec.n_traces
     units, secs, runs, used = 0, 0.0, 0, 1
+    level_s = [0.0] * (max_size + 1)
     while secs < target_s or runs == 0:
         t0 = time.perf_counter()
         r = learn(spec.P, spec.N, spec.n_props, max_size=max_size, stop_mode=0)
@@ -294,7 +296,10 @@ def _oracle_rate(learn, spec, max_size, target_s):
         units += sum(r["candidates"][1:max_size + 1]) * T
         runs += 1
         used = r.get("threads", 1)
-    return units / secs, runs, secs, used
+        for k in range(1, max_size + 1):
+            level_s[k] += r["seconds"][k]
+    level_ms = [round(1e3 * level_s[k] / runs, 3) for k in range(1, max_size + 1)]
+    return units / secs, runs, secs, used, level_ms
 
 
 def cpu_baseline(target_s: float = 10.0, max_size: int = 6):
@@ -306,16 +311,20 @@ def cpu_baseline(target_s: float = 10.0, max_size: int = 6):
     spec = synth.single_large()
     sample = "single_large traces (2048), sizes 1..%d enumerated completely, %d run(s), %.1f s"
     unit = METRIC.split("/")[0] + "/s"
-    v1, runs1, secs1, _ = _oracle_rate(O.learn, spec, max_size, target_s)
-    single = {"value": v1, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample % (max_size, runs1, secs1)}
+    v1, runs1, secs1, _, lv1 = _oracle_rate(O.learn, spec, max_size, target_s)
+    single = {"value": v1, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample % (max_size, runs1, secs1),
+              "level_ms": lv1, "total_ms": round(sum(lv1), 3)}
     try:
-        vn, runsn, secsn, used = _oracle_rate(O.learn_par, spec, max_size, target_s)
+        vn, runsn, secsn, used, lvn = _oracle_rate(O.learn_par, spec, max_size, target_s)
     except Exception as e:   # no OpenMP toolchain: the single-core figure stands alone
         single["multi_core_unavailable"] = str(e)[:200]
         return single
     return {"value": vn, "unit": unit, "cores": used, "kind": "oracle",
             "sample": sample % (max_size, runsn, secsn) + " (OpenMP over each block of a level's candidates, "
                       "admitted in enumeration order)",
+            "level_ms": lvn, "total_ms": round(sum(lvn), 3),
+            "level_ms_note": "the oracle's time per size level 1..%d on the same traces (mean over its runs); the "
+                             "GPU's per level are levels.ms" % max_size,
             "nproc": os.cpu_count(), "single_core": single}
 
 
