@@ -1102,7 +1102,11 @@ public:
             for (int i : groups[g].seg_ids) gcands[g] += seg_candidates(segs[i]);
             round_cands += gcands[g];
         }
-        const bool concurrent = groups.size() > 1 && round_cands < kConcurrentBelow;
+        // launches run concurrently in small rounds (bound by launch latency)
+        // and whenever the round holds several problems (batches, servers:
+        // many launch shapes, each launch small); a large round of one problem
+        // keeps its launches in order, so that each has an event time of its own
+        const bool concurrent = groups.size() > 1 && (round_cands < kConcurrentBelow || ran.size() > 1);
         std::vector<int> choice(groups.size(), -1);
         std::vector<std::string> tkey(groups.size());
         for (size_t g = 0; g < groups.size(); ++g) {
