@@ -41,6 +41,8 @@ constexpr int kMaxGroups = 512;                       // launches per round
 // hash set).  Larger rounds run their launches one after another, so each
 // launch's time is its own.
 constexpr uint64_t kConcurrentBelow = 1ull << 17;
+// host-planned rounds of one problem below this many candidates run their launches concurrently
+constexpr uint64_t kRoundConcurrentBelow = 1ull << 18;
 constexpr int kAuxStreams = 8;
 // A chain of device-planned levels becomes a CUDA graph the eighth time its
 // shape is enqueued; up to this many shapes are kept.
@@ -1106,7 +1108,7 @@ public:
         // and whenever the round holds several problems (batches, servers:
         // many launch shapes, each launch small); a large round of one problem
         // keeps its launches in order, so that each has an event time of its own
-        const bool concurrent = groups.size() > 1 && (round_cands < kConcurrentBelow || ran.size() > 1);
+        const bool concurrent = groups.size() > 1 && (round_cands < kRoundConcurrentBelow || ran.size() > 1);
         std::vector<int> choice(groups.size(), -1);
         std::vector<std::string> tkey(groups.size());
         for (size_t g = 0; g < groups.size(); ++g) {
