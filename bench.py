@@ -747,7 +747,8 @@ def main():
 
     # dominant kernel: the (size level, connective) launch with the longest
     # device time (CUDA events the library records on its stream)
-    pairs = [(k, o) for k in range(1, r0["levels_done"] + 1) for o in range(8)]
+    # (only launches that ran alone, whose event time is their own)
+    pairs = [(k, o) for k in range(1, r0["levels_done"] + 1) for o in range(8) if r0["op_alone"][k][o]]
     kd, od = max(pairs, key=lambda ko: sum(r["op_ms"][ko[0]][ko[1]] for r in results))
     kd_ms = statistics.mean(r["op_ms"][kd][od] for r in results)
     per_trace = 4 if r0["traces_per_word"] == 2 else 8 * W
@@ -869,7 +870,8 @@ def main():
                  "value": sum(units_of(x, T) for x in alt_res) / (sum(alt_times) / 1e3),
                  "dominant_launch_ms": statistics.mean(x["op_ms"][kd][od] for x in alt_res),
                  "top_level_op_ms": {name: round(statistics.mean(x["op_ms"][K][op] for x in alt_res), 4)
-                                     for op, name in enumerate(OP_NAMES) if op > 0},
+                                     for op, name in enumerate(OP_NAMES) if op > 0 and alt_res[0]["op_alone"][K][op]},
+                 "top_level_ms": round(statistics.mean(x["ms"][K] for x in alt_res), 4),
                  "same_counts": all(x["unique"] == r0["unique"] and x["candidates"] == r0["candidates"]
                                     for x in alt_res)}
 
@@ -894,8 +896,16 @@ def main():
             "levels": {"unique": r0["unique"][1:], "candidates": r0["candidates"][1:],
                        "device_planned": r0["device_planned_levels"], "from_cuda_graph": r0["graph_levels"],
                        "ms": [round(x, 4) for x in r0["ms"][1:]], "entries": r0["entries"],
+                       # own launch times of the last level's connectives that ran alone; the
+                       # others ran concurrently after them (the level's time covers both)
                        "top_level_op_ms": {name: round(statistics.mean(r["op_ms"][K][op] for r in results), 4)
-                                           for op, name in enumerate(OP_NAMES) if r0["op_ms"][K][op] > 0}},
+                                           for op, name in enumerate(OP_NAMES)
+                                           if r0["op_ms"][K][op] > 0 and r0["op_alone"][K][op]},
+                       "top_level_concurrent": [name for op, name in enumerate(OP_NAMES)
+                                                if r0["op_ms"][K][op] > 0 and not r0["op_alone"][K][op]],
+                       "top_level_concurrent_ms": round(statistics.mean(
+                           r["ms"][K] - sum(r["op_ms"][K][op] for op in range(8) if r["op_alone"][K][op])
+                           for r in results), 4)},
             "roofline": roofline,
             "kernel_ms_per_step": statistics.mean(kernel_ms),
             "value_by_kernel_time": local_units / (sum(kernel_ms) / 1e3),

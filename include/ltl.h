@@ -225,10 +225,15 @@ typedef struct {
     float op_ms[LTL_MAX_LEVELS][8];       /* device time of each connective's
                                              launch: [level][op], op = 0 atoms,
                                              1 Not, 2 And, 3 Or, 4 X, 5 F, 6 G,
-                                             7 U.  Levels of fewer than 2^17
-                                             candidates run their launches
-                                             concurrently; there it is the time
-                                             from the level's start.  Levels
+                                             7 U.  Its own time where op_alone
+                                             is set.  Levels that run their
+                                             launches concurrently (fewer than
+                                             2^18 candidates, or several
+                                             problems): the time from the
+                                             level's start.  Larger levels of
+                                             one problem run U alone first, then
+                                             the others concurrently: theirs is
+                                             the time from U's end.  Levels
                                              planned on the device
                                              (LTL_PLAN_AUTO) are timed by the
                                              device clock from one planner
@@ -252,6 +257,9 @@ typedef struct {
     uint8_t op_kernel[LTL_MAX_LEVELS][8]; /* which level kernel ran each
                                              launch ([level][op] as op_ms):
                                              LTL_LAUNCH_*, 0 where none ran   */
+    uint8_t op_alone[LTL_MAX_LEVELS][8];  /* 1 where the launch ran alone on the
+                                             device, so that op_ms is its own
+                                             duration                          */
 } ltl_stats;
 
 /* op_kernel values */

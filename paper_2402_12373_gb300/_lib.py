@@ -90,7 +90,8 @@ class Stats(ctypes.Structure):
                 ("device_planned_levels", ctypes.c_uint32), ("graph_levels", ctypes.c_uint32),
                 ("compares", ctypes.c_uint64), ("collisions", ctypes.c_uint64),
                 ("op_staged", (ctypes.c_uint64 * 8) * MAX_LEVELS),
-                ("op_kernel", (ctypes.c_uint8 * 8) * MAX_LEVELS)]
+                ("op_kernel", (ctypes.c_uint8 * 8) * MAX_LEVELS),
+                ("op_alone", (ctypes.c_uint8 * 8) * MAX_LEVELS)]
 
     def to_dict(self, max_size: int) -> Dict:
         K = max_size
@@ -112,6 +113,7 @@ class Stats(ctypes.Structure):
             "compares": int(self.compares), "collisions": int(self.collisions),
             "op_staged": [[int(self.op_staged[c][o]) for o in range(8)] for c in range(K + 1)],
             "op_kernel": [[LAUNCH_KINDS[int(self.op_kernel[c][o])] for o in range(8)] for c in range(K + 1)],
+            "op_alone": [[bool(self.op_alone[c][o]) for o in range(8)] for c in range(K + 1)],
         }
 
 

@@ -1109,6 +1109,14 @@ public:
         // many launch shapes, each launch small); a large round of one problem
         // keeps its launches in order, so that each has an event time of its own
         const bool concurrent = groups.size() > 1 && (round_cands < kRoundConcurrentBelow || ran.size() > 1);
+        // a larger round of one problem: its U launch, the level's longest, runs
+        // alone first, timed by its own events; the other launches follow it
+        // concurrently (in order their tails add up)
+        int lead = -1;
+        if (!concurrent && groups.size() > 2)
+            for (size_t g = 0; g < groups.size(); ++g)
+                if (groups[g].op == OP_U && (lead < 0 || gcands[g] > gcands[lead])) lead = (int)g;
+        const bool split = lead >= 0;
         std::vector<int> choice(groups.size(), -1);
         std::vector<std::string> tkey(groups.size());
         for (size_t g = 0; g < groups.size(); ++g) {
@@ -1118,7 +1126,8 @@ public:
             if (st != LTL_OK) return st;
             const uint64_t cands = gcands[g];
             int c = kTuneDefault;
-            if (tuner.enabled && !concurrent && cands >= kTuneMinCands) {
+            // launches that run alone are tuned (their event times are their own)
+            if (tuner.enabled && !concurrent && (!split || (int)g == lead) && cands >= kTuneMinCands) {
                 const Slot &s0 = slots[segs[gr.seg_ids[0]].prob];
                 char key[96];
                 snprintf(key, sizeof key, "%s%dc%dt%d%s-op%d-b%d", s0.L.narrow ? "n" : "w", s0.L.Wt, s0.L.C, gr.nt,
@@ -1158,13 +1167,19 @@ public:
         LTL_CUDA_TRY(cudaMemcpyAsync(d_segs, h_segs, sizeof(Seg) * n_out, cudaMemcpyHostToDevice, stream));
         LTL_CUDA_TRY(cudaMemsetAsync(d_counters, 0, sizeof(unsigned long long) * 2 * kMaxGroups, stream));
         LTL_CUDA_TRY(cudaEventRecord(ev_begin, stream));
-        if (concurrent)
+        if (concurrent || split)
             while ((int)aux.size() < kAuxStreams) {
                 cudaStream_t st = nullptr;
                 LTL_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
                 aux.push_back(st);
             }
-        for (size_t g = 0; g < groups.size(); ++g) {
+        // launch order: the lead launch first when the round is split
+        std::vector<size_t> order;
+        if (split) order.push_back((size_t)lead);
+        for (size_t g = 0; g < groups.size(); ++g)
+            if ((int)g != lead) order.push_back(g);
+        for (size_t oi = 0; oi < order.size(); ++oi) {
+            const size_t g = order[oi];
             LevelArgs la{};
             la.segs = d_segs + first[g];
             la.probs = (const Problem *)(ws + o_probs);
@@ -1177,6 +1192,9 @@ public:
             if (concurrent) {
                 st = aux[g % aux.size()];
                 LTL_CUDA_TRY(cudaStreamWaitEvent(st, ev_begin, 0));
+            } else if (split && (int)g != lead) {
+                st = aux[oi % aux.size()];
+                LTL_CUDA_TRY(cudaStreamWaitEvent(st, ev_op[lead], 0));
             }
             if (grid[g] > 0 && groups[g].cl) {
                 // grid[g] clusters of cl CTAs
@@ -1198,8 +1216,9 @@ public:
             }
             LTL_CUDA_TRY(cudaEventRecord(ev_op[g], st));
         }
-        if (concurrent)
-            for (size_t g = 0; g < groups.size(); ++g) LTL_CUDA_TRY(cudaStreamWaitEvent(stream, ev_op[g], 0));
+        if (concurrent || split)
+            for (size_t g = 0; g < groups.size(); ++g)
+                if ((int)g != lead) LTL_CUDA_TRY(cudaStreamWaitEvent(stream, ev_op[g], 0));
         int hi = 0;
         for (int si : ran) hi = std::max(hi, si + 1);
         LTL_CUDA_TRY(cudaMemcpyAsync(h_ctrls, ws + o_ctrls, sizeof(Ctrl) * hi, cudaMemcpyDeviceToHost, stream));
@@ -1207,13 +1226,18 @@ public:
                                      cudaMemcpyDeviceToHost, stream));
         LTL_CUDA_TRY(cudaStreamSynchronize(stream));
         ++total_rounds;
-        // per launch: its own time when launches ran one after another; from
-        // the start of the round when they ran concurrently
+        // per launch: its own time when launches ran one after another (the
+        // lead launch of a split round included); from the start of the round
+        // when they ran concurrently; from the end of the lead launch for the
+        // others of a split round
         float round_ms = 0.f;
         std::vector<float> op_ms(groups.size());
         for (size_t g = 0; g < groups.size(); ++g) {
             float t = 0.f;
-            LTL_CUDA_TRY(cudaEventElapsedTime(&t, (g == 0 || concurrent) ? ev_begin : ev_op[g - 1], ev_op[g]));
+            cudaEvent_t from = ev_begin;
+            if (split) from = (int)g == lead ? ev_begin : ev_op[lead];
+            else if (!concurrent && g > 0) from = ev_op[g - 1];
+            LTL_CUDA_TRY(cudaEventElapsedTime(&t, from, ev_op[g]));
             op_ms[g] = t;
             if (choice[g] >= 0) tuner.record(tkey[g], choice[g], 1e6 * (double)t / (double)gcands[g]);
             float since = 0.f;
@@ -1232,6 +1256,7 @@ public:
                     if (segs[i].prob == si) {
                         s.st.op_ms[k][groups[g].op] = op_ms[g];
                         s.st.op_kernel[k][groups[g].op] = (uint8_t)groups[g].kind;
+                        s.st.op_alone[k][groups[g].op] = (!concurrent && (!split || (int)g == lead)) ? 1 : 0;
                         s.st.op_staged[k][groups[g].op] = h_staged[g];
                         break;
                     }

@@ -29,11 +29,11 @@ def _classes(dump):
 
 
 def test_tuning_changes_no_result(ws, tmp_path):
-    """Size 8 has the first level launched alone (more than 2^17 candidates),
-    so its launches are tuned; every tuned call equals the untuned one, which
-    equals the oracle up to size 6."""
+    """Size 9 is the first level with a launch that runs alone (its U launch:
+    the level has at least 2^18 candidates), so that launch is tuned; every
+    tuned call equals the untuned one, which equals the oracle up to size 6."""
     s = synth.single_large(n_each=512)
-    K = 8
+    K = 9
     want6 = O.learn(s.P, s.N, 3, max_size=6, stop_mode=0)
     with L.Context(workspace=ws, stop=L.STOP_NONE) as ctx:
         want = ctx.learn(s.P, s.N, 3, max_size=K)

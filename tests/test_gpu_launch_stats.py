@@ -75,3 +75,19 @@ def test_forced_fused_kernel_reports_it():
         for op in range(1, 8):
             if r["op_ms"][k][op] > 0:
                 assert r["op_kernel"][k][op] == "fused_level_kernel", (k, op)
+
+
+def test_which_launches_ran_alone():
+    """op_alone marks the launches whose op_ms is their own duration: in a
+    level of one problem with at least 2^18 candidates U runs alone first and
+    the other connectives after it concurrently; smaller levels run their
+    launches concurrently (or, planned on the device, in a chain)."""
+    s = synth.single_large()
+    ws = L.default_workspace(16 << 30)
+    with L.Context(workspace=ws, stop=L.STOP_NONE, mem_budget=10 << 30) as ctx:
+        r = ctx.learn(s.P, s.N, 3, max_size=9)
+    assert r["levels_done"] == 9 and r["candidates"][9] >= 1 << 18 and r["candidates"][8] < 1 << 18
+    alone = r["op_alone"]
+    assert alone[9][7] and not any(alone[9][op] for op in range(1, 7))
+    assert not any(alone[k][op] for k in range(1, 9) for op in range(8))
+    assert r["op_ms"][9][7] > 0 and r["op_ms"][9][7] <= r["ms"][9]
