@@ -119,7 +119,7 @@ public:
         if (total) LTL_CUDA_TRY(cudaMemcpyAsync(base + o_let, letters.data(), 4 * total, cudaMemcpyHostToDevice, sm));
         LTL_CUDA_TRY(cudaMemcpyAsync(base + o_off, offsets.data(), 8 * (T + 1), cudaMemcpyHostToDevice, sm));
         LTL_CUDA_TRY(launch_pack((const uint32_t *)(base + o_let), (const uint64_t *)(base + o_off), (uint32_t)T, plane,
-                                 W, n_props, (uint64_t *)(base + o_mask), (uint64_t *)(base + o_atoms), stride,
+                                 W, Wt, n_props, (uint64_t *)(base + o_mask), (uint64_t *)(base + o_atoms), stride,
                                  (Ctrl *)(base + o_ctrl), sm));
         Ctrl h;
         LTL_CUDA_TRY(cudaMemcpyAsync(&h, base + o_ctrl, sizeof h, cudaMemcpyDeviceToHost, sm));

@@ -653,16 +653,14 @@ public:
         uint64_t *d_atoms = (uint64_t *)(base + L.o_atoms);
         LTL_CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
         LTL_CUDA_TRY(cudaMemsetAsync(base + L.o_hslots, 0, sizeof(HSlot) * L.hslots, stream));
-        LTL_CUDA_TRY(cudaMemsetAsync(d_mask, 0, 8 * L.stride, stream));
-        LTL_CUDA_TRY(cudaMemsetAsync(d_atoms, 0, 8 * L.stride * (uint64_t)L.n_props, stream));
+        // the pack kernel writes every word of the mask, the atoms and the NH keys
         if (L.narrow)
             LTL_CUDA_TRY(launch_pack_narrow(d_letters, d_offsets, (uint32_t)T, L.plane, L.n_props, d_mask, d_atoms,
-                                            L.stride, d_ctrl, stream));
+                                            L.stride, d_ctrl, stream, d_keys, kKeySeed));
         else
-            LTL_CUDA_TRY(launch_pack(d_letters, d_offsets, (uint32_t)T, L.plane, L.W, L.n_props, d_mask, d_atoms,
-                                     L.stride, d_ctrl, stream));
-        LTL_CUDA_TRY(launch_keys(d_keys, L.stride, kKeySeed, stream));
-        s.st.launches += 2;
+            LTL_CUDA_TRY(launch_pack(d_letters, d_offsets, (uint32_t)T, L.plane, L.W, L.Wt, L.n_props, d_mask, d_atoms,
+                                     L.stride, d_ctrl, stream, d_keys, kKeySeed));
+        s.st.launches += 1;
         Problem &pb = h_probs[si];
         pb = Problem{};
         pb.arena = (uint64_t *)(base + L.o_arena);

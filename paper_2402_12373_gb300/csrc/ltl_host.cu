@@ -270,16 +270,8 @@ ltl_status ltl_eval(const char *formula, const ltl_traces *traces, int n_props, 
     if (total_pos) EVAL_TRY(cudaMemcpyAsync(d + o_let, traces->letters, 4 * total_pos, cudaMemcpyHostToDevice, sm));
     EVAL_TRY(cudaMemcpyAsync(d + o_off, traces->offsets, 8 * (T + 1), cudaMemcpyHostToDevice, sm));
     EVAL_TRY(cudaMemcpyAsync(d + o_prog, prog.data(), 4 * prog.size(), cudaMemcpyHostToDevice, sm));
-    EVAL_TRY(launch_pack((const uint32_t *)(d + o_let), (const uint64_t *)(d + o_off), (uint32_t)T, plane, W, n_props,
+    EVAL_TRY(launch_pack((const uint32_t *)(d + o_let), (const uint64_t *)(d + o_off), (uint32_t)T, plane, W, Wt, n_props,
                          (uint64_t *)(d + o_mask), (uint64_t *)(d + o_atoms), stride, (Ctrl *)(d + o_ctrl), sm));
-    if (Wt > W) {
-        // planes W..Wt-1 are padding: zero them for the operators
-        for (int w = W; w < Wt; ++w) {
-            EVAL_TRY(cudaMemsetAsync(d + o_mask + 8 * plane * w, 0, 8 * plane, sm));
-            for (int p = 0; p < n_props; ++p)
-                EVAL_TRY(cudaMemsetAsync(d + o_atoms + 8 * (stride * p + plane * w), 0, 8 * plane, sm));
-        }
-    }
     EVAL_TRY(launch_eval(Wt, (const uint32_t *)(d + o_prog), (int)prog.size(), (const uint64_t *)(d + o_atoms),
                          (const uint64_t *)(d + o_mask), stride, plane, (uint64_t *)(d + o_stack), ceil_log2(ml),
                          (uint32_t)T, (uint64_t *)(d + o_out), words_per_trace, sm));

@@ -11,26 +11,38 @@
 namespace ltl {
 
 // ---------------------------------------------------------------------------
-// Trace packing: length masks and the atoms' characteristic matrices.  One
-// thread per (plane w, trace slot t).  Positions are read straight from the
+// Trace packing: length masks and the atoms' characteristic matrices (and,
+// given `keys`, the NH fingerprint keys, one per matrix word).  One thread per
+// (plane w < Wt, trace slot t); every word of the mask, the atoms and the keys
+// is written, the padding planes W..Wt-1 as zeros, so none needs clearing
+// first.  Positions are read straight from the
 // concatenated letters; a letter with a bit >= n_props, a decreasing offset
-// or a trace longer than 64 * W marks the input invalid.
+// or a trace longer than 64 * W marks the input invalid (a trace with bad
+// offsets is then packed as empty).
 // ---------------------------------------------------------------------------
+
+// NH key of matrix word i: a SplitMix64 output of a fixed seed.
+__device__ __forceinline__ uint64_t nh_key(uint64_t seed, uint64_t i) {
+    return mix64(seed + (i + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
 __global__ void pack_kernel(const uint32_t *__restrict__ letters, const uint64_t *__restrict__ offsets,
-                            uint32_t n_traces, uint64_t plane, int W, int n_props, uint64_t *mask,
-                            uint64_t *atoms, uint64_t stride, Ctrl *ctrl) {
+                            uint32_t n_traces, uint64_t plane, int W, int Wt, int n_props, uint64_t *mask,
+                            uint64_t *atoms, uint64_t stride, Ctrl *ctrl, uint64_t *keys, uint64_t seed) {
     const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= plane * (uint64_t)W) return;
+    if (idx >= plane * (uint64_t)Wt) return;
+    if (keys) keys[idx] = nh_key(seed, idx);
     const uint64_t t = idx % plane, w = idx / plane;
     uint64_t off = 0, len = 0;
     if (t < n_traces) {
         off = offsets[t];
         const uint64_t end = offsets[t + 1];
-        if (end < off || (t == 0 && off != 0)) {
+        if (end < off || (t == 0 && off != 0)) {   // no letter of it is read
             atomicExch(&ctrl->invalid_letter, 1);
-            return;
+            off = 0;
+        } else {
+            len = end - off;
         }
-        len = end - off;
         if (len > 64ull * (uint64_t)W) {
             atomicExch(&ctrl->invalid_letter, 1);
             len = 64ull * (uint64_t)W;
@@ -56,20 +68,22 @@ __global__ void pack_kernel(const uint32_t *__restrict__ letters, const uint64_t
 // 2q (bits 0..31) and 2q + 1 (bits 32..63).  One thread per word.
 __global__ void pack_narrow_kernel(const uint32_t *__restrict__ letters, const uint64_t *__restrict__ offsets,
                                    uint32_t n_traces, uint64_t plane, int n_props, uint64_t *mask, uint64_t *atoms,
-                                   uint64_t stride, Ctrl *ctrl) {
+                                   uint64_t stride, Ctrl *ctrl, uint64_t *keys, uint64_t seed) {
     const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= plane) return;
+    if (keys) keys[q] = nh_key(seed, q);
     uint64_t off[2] = {0, 0}, len[2] = {0, 0};
     for (int h = 0; h < 2; ++h) {
         const uint64_t t = 2 * q + h;
         if (t < n_traces) {
             off[h] = offsets[t];
             const uint64_t end = offsets[t + 1];
-            if (end < off[h] || (t == 0 && off[h] != 0)) {
+            if (end < off[h] || (t == 0 && off[h] != 0)) {   // no letter of it is read
                 atomicExch(&ctrl->invalid_letter, 1);
-                return;
+                off[h] = 0;
+            } else {
+                len[h] = end - off[h];
             }
-            len[h] = end - off[h];
             if (len[h] > 32) {
                 atomicExch(&ctrl->invalid_letter, 1);
                 len[h] = 32;
@@ -91,12 +105,6 @@ __global__ void pack_narrow_kernel(const uint32_t *__restrict__ letters, const u
         atoms[(uint64_t)p * stride + q] = bits;
     }
     if (n_props < 32 && (seen >> n_props)) atomicExch(&ctrl->invalid_letter, 1);
-}
-
-// NH keys, one per word of a matrix: SplitMix64 outputs of a fixed seed.
-__global__ void keys_kernel(uint64_t *keys, uint64_t n, uint64_t seed) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) keys[i] = mix64(seed + (i + 1) * 0x9E3779B97F4A7C15ULL);
 }
 
 // ---------------------------------------------------------------------------
@@ -216,27 +224,21 @@ __global__ void unpack_kernel(const uint64_t *src, uint64_t plane, int W, uint32
 // ---------------------------------------------------------------------------
 
 cudaError_t launch_pack(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
-                        int W, int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
-                        cudaStream_t s) {
-    const uint64_t n = plane * (uint64_t)W;
+                        int W, int Wt, int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
+                        cudaStream_t s, uint64_t *keys, uint64_t seed) {
+    const uint64_t n = plane * (uint64_t)Wt;
     const int th = 256;
-    pack_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(letters, offsets, n_traces, plane, W, n_props, mask,
-                                                             atoms, stride, ctrl);
+    pack_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(letters, offsets, n_traces, plane, W, Wt, n_props,
+                                                             mask, atoms, stride, ctrl, keys, seed);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_narrow(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
                                int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
-                               cudaStream_t s) {
+                               cudaStream_t s, uint64_t *keys, uint64_t seed) {
     const int th = 256;
     pack_narrow_kernel<<<(unsigned)((plane + th - 1) / th), th, 0, s>>>(letters, offsets, n_traces, plane, n_props,
-                                                                        mask, atoms, stride, ctrl);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_keys(uint64_t *keys, uint64_t n, uint64_t seed, cudaStream_t s) {
-    const int th = 256;
-    keys_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(keys, n, seed);
+                                                                        mask, atoms, stride, ctrl, keys, seed);
     return cudaGetLastError();
 }
 

@@ -119,12 +119,11 @@ extern "C" ltl_status ltl_eval_noalloc(const char *formula, const uint32_t *d_le
             return set_error(LTL_ERR_CUDA, m_.c_str());                                \
         }                                                                              \
     } while (0)
-    // what must start at zero: the control word, and the mask / atom planes
-    // (padding planes and padding traces are read by the operators)
+    // what must start at zero: the control word (the pack kernel writes every
+    // word of the mask and atom planes, padding planes and traces included)
     NOALLOC_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), sm));
-    NOALLOC_TRY(cudaMemsetAsync(mask, 0, (size_t)(o_stack - o_mask), sm));
     NOALLOC_TRY(cudaMemcpyAsync(scr + o_prog, prog.data(), 4 * prog.size(), cudaMemcpyHostToDevice, sm));
-    NOALLOC_TRY(launch_pack(d_letters, d_offsets, (uint32_t)n_traces, plane, W, n_props, mask, atoms, stride, ctrl, sm));
+    NOALLOC_TRY(launch_pack(d_letters, d_offsets, (uint32_t)n_traces, plane, W, Wt, n_props, mask, atoms, stride, ctrl, sm));
     // log steps for the packed capacity (64 * W positions), not for max_len:
     // the pack kernel accepts any trace that fits W words, and a trace longer
     // than max_len evaluated with max_len's steps would lose the F / G / U
