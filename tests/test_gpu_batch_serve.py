@@ -130,8 +130,15 @@ def test_server_alone_vs_mix(ws):
 # propositions, minimal sizes 1..7, max size = planted size + 2.
 BATCH_SLICE = [0, 1, 2, 3, 4, 5, 8, 10, 11, 15, 16, 22, 23, 30, 36, 37, 38, 40, 44, 45, 49, 50, 51, 56,
                59, 63]
-# Seeds of the served workload's trace-scaling problems (65536 traces each).
-SERVED_SEEDS = [1000, 1001, 1002, 1003]
+# Seeds of the served workload's trace-scaling problems (65536 traces each):
+# the benchmark's whole served pool.  Seven of them separate at size 3; the
+# eighth (seed 1004) has no separator up to size 3 and fills its 2 GiB cache
+# before the oracle's minimal size, which the oracle (O(n^2) U over 65,536
+# traces) takes minutes to reach.  So the oracle enumerates the served
+# problems up to SERVED_ORACLE_SIZE, and a problem it does not solve there is
+# checked level by level up to that size.
+SERVED_SEEDS = list(range(1000, 1008))
+SERVED_ORACLE_SIZE = 3
 
 
 def _spec(kind, i):
@@ -147,7 +154,8 @@ def _oracle_job(kind, i):
     spawn-started worker process."""
     from oracle import oracle as Oc
     sp = _spec(kind, i)
-    return Oc.learn(sp.P, sp.N, sp.n_props, max_size=_max_size(kind, sp), stop_mode=1)
+    K = _max_size(kind, sp) if kind == "batched" else SERVED_ORACLE_SIZE
+    return Oc.learn(sp.P, sp.N, sp.n_props, max_size=K, stop_mode=1)
 
 
 @pytest.fixture(scope="module")
@@ -169,6 +177,23 @@ def _equals_oracle(got, want, sp):
     if got["status"] == "found":
         assert O.separates(got["formula"], sp.P, sp.N, sp.n_props), got["formula"]
         assert O.size(got["formula"]) == got["size"]
+
+
+def _equals_oracle_up_to(got, want, sp, K):
+    """`want` is the oracle's result with sizes up to K.  Found there: the
+    same result.  Not found: levels 1..K are complete on both sides with the
+    same counts, and the GPU's separator, if any, is larger than K."""
+    if want["status"] == "found":
+        _equals_oracle(got, want, sp)
+        return
+    assert want["status"] == "not_found" and want["levels_done"] == K
+    assert got["levels_done"] >= K
+    assert got["unique"][1:K + 1] == want["unique"][1:K + 1]
+    assert got["candidates"][1:K + 1] == want["candidates"][1:K + 1]
+    assert got["status"] in ("found", "cap", "not_found"), got["status"]
+    if got["status"] == "found":
+        assert got["size"] > K
+        assert O.separates(got["formula"], sp.P, sp.N, sp.n_props), got["formula"]
 
 
 def _budgets(ws, specs):
@@ -216,11 +241,11 @@ def test_served_batched_slice_equals_oracle(ws, oracle_results):
 
 
 def test_served_trace_scaling_requests_equal_oracle(oracle_results):
-    """Config-5-shaped requests (65536 two-word traces each, 2 GiB per
+    """The served workload's requests (65536 two-word traces each, 2 GiB per
     problem as in the benchmark) through the continuous-batching server."""
     big = L.default_workspace(12 << 30)
     specs = [_spec("served", s) for s in SERVED_SEEDS]
     got = _serve(big, specs, "served", [2 << 30] * len(specs), 2)
     for s, sp, r in zip(SERVED_SEEDS, specs, got):
-        _equals_oracle(r, oracle_results[("served", s)], sp)
+        _equals_oracle_up_to(r, oracle_results[("served", s)], sp, SERVED_ORACLE_SIZE)
     del big
