@@ -261,25 +261,37 @@ class ClockSampler:
                 "samples": len(sm), "interval_ms": 50}
 
 
-def autotune_summary(ctx, off):
+# Launch configurations the library's tuner tries per launch class (2, 4 or 8
+# tiles per resident CTA, at the occupancy maximum or one CTA per SM fewer),
+# one untried configuration per launch of the class.  A step launches each
+# tuned class once, so this many calls end the exploration.
+AUTOTUNE_CONFIGS = 6
+
+
+def autotune_summary(ctx, off, calls):
     """The tuned launch classes: chosen configuration (tiles per resident CTA,
     CTAs per SM below the occupancy maximum) and its best time per candidate
     against the default configuration's (4 tiles per CTA, full occupancy)."""
     if off:
         return {"enabled": False}
     tpc = [2, 4, 8, 2, 4, 8]
+    assert len(tpc) == AUTOTUNE_CONFIGS
     less = [0, 0, 0, 1, 1, 1]
     chosen = {}
     for line in ctx.autotune_dump().strip().splitlines():
         parts = line.split()
         conf = [tuple(map(float, p.split(":"))) for p in parts[1:]]
+        assert len(conf) == AUTOTUNE_CONFIGS, line
         tried = [(v, c) for c, (v, n) in enumerate(conf) if n > 0]
         if not tried:
             continue
         v, c = min(tried)
         chosen[parts[0]] = {"tiles_per_cta": tpc[c], "ctas_per_sm_less": less[c], "ns_per_candidate": round(v, 3),
                             "default_ns_per_candidate": round(conf[1][0], 3) if conf[1][1] else None}
-    return {"enabled": True, "classes": chosen}
+    return {"enabled": True, "tuning_calls": calls,
+            "tuning": "the tuner tries its configurations in untimed calls before the warm-up steps; the warm-up and "
+                      "timed steps run the fastest",
+            "classes": chosen}
 
 
 def _oracle_rate(learn, spec, max_size, target_s):
@@ -629,7 +641,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=8,
-                    help="untimed steps (at least 3); the launch autotuner tries its configurations in them")
+                    help="untimed steps (at least 3), after the autotuner's untimed tuning calls")
     ap.add_argument("--no-autotune", action="store_true", help="fixed launch heuristics instead of the autotuner")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-size", type=int, default=MAX_SIZE)
@@ -699,7 +711,8 @@ def main():
         return ctx.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
 
     int_peak = L.int32_peak()   # integer roof, measured before the warm-up
-    for _ in range(args.warmup):
+    tune_calls = 0 if args.no_autotune else AUTOTUNE_CONFIGS
+    for _ in range(tune_calls + args.warmup):
         step()
         flush.zero_()
     torch.cuda.synchronize()
@@ -849,7 +862,7 @@ def main():
         alt = L.PROP_LOGSTEP if L.DEFAULT_PROPAGATION == L.PROP_CARRY else L.PROP_CARRY
         ctx_alt = L.Context(workspace=ws, stop=L.STOP_NONE, max_chunks=args.max_chunks, mem_budget=budget,
                             autotune=None if args.no_autotune else "", propagation=alt)
-        for _ in range(args.warmup):
+        for _ in range(tune_calls + args.warmup):
             ctx_alt.learn_device(d_letters, d_offsets, spec.P.n, spec.N.n, max_len, spec.n_props, max_size=K)
             flush.zero_()
         alt_times, alt_res = [], []
@@ -914,7 +927,7 @@ def main():
                                  "formula": found["formula"], "mode": "stop at first separator, host buffers"},
             "gpu_launches": launches,
             "clocks": clocks,
-            "autotune": autotune_summary(ctx, args.no_autotune),
+            "autotune": autotune_summary(ctx, args.no_autotune, tune_calls),
         }
         if other is not None:
             out["other_propagation"] = other
