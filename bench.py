@@ -428,7 +428,7 @@ def bench_served(L, ws, pool, rates=(0.5, 0.9, 1.5), per_rate_s=1.5, seed=5):
     out = {"workload": "served: Poisson arrivals of trace-scaling problems (65536 traces, length U{33..128}, "
                        "4 props, planted (((p0 U p1) & G !p3) & F p2), seeds 1000..%d cycled), max size 11, "
                        "stop at first separator, 2 GiB per problem; each server gets one untimed warm-up "
-                       "request before the timed arrivals" % (1000 + len(pool) - 1),
+                       "request of every problem of the pool before the timed arrivals" % (1000 + len(pool) - 1),
            "one_at_a_time_problems_per_s": mu, "rates": []}
     rng = _random.Random(seed)
     for f in rates:
@@ -442,13 +442,15 @@ def bench_served(L, ws, pool, rates=(0.5, 0.9, 1.5), per_rate_s=1.5, seed=5):
             arrivals.append(acc)
         results = {}
         with L.Server(workspace=ws, stop=L.STOP_FIRST, max_resident=64, mem_budget=2 << 30) as srv:
-            # one untimed request first: a fresh server's first admission pays
-            # one-time set-up (launch attributes, occupancy queries, events)
-            sp = pool[0]
-            warm = srv.submit(sp.P, sp.N, sp.n_props, max_size=11)
+            # untimed requests first, one of every problem of the pool: a fresh
+            # server's first admissions and the first rounds of each shape
+            # pay one-time set-up (launch attributes, occupancy queries,
+            # events, the first launch of each kernel)
+            warm = {srv.submit(sp.P, sp.N, sp.n_props, max_size=11) for sp in pool}
             t_w = time.perf_counter()
-            while time.perf_counter() - t_w < 60 and not any(r["id"] == warm for r in srv.poll(8, 50)):
-                pass
+            while warm and time.perf_counter() - t_w < 60:
+                for r in srv.poll(64, 50):
+                    warm.discard(r["id"])
             ids = {}
             t_start = time.perf_counter()
 
