@@ -201,6 +201,33 @@ def test_learn_device_input_matches_host_input(ws):
     assert a["unique"] == b["unique"] and a["candidates"] == b["candidates"] and a["size"] == b["size"]
 
 
+def test_learn_device_input_with_bad_offsets_is_rejected(ws):
+    """Device-resident offsets that decrease, or that do not start at 0: the
+    pack kernel packs such a trace as empty (it reads none of its letters) and
+    flags the input, the call returns LTL_ERR_INVALID, and the same context
+    then learns a valid input exactly.  Every offset stays inside the letter
+    buffer."""
+    s = synth.plain_single(seed=2)
+    letters = np.concatenate([s.P.letters, s.N.letters]).astype(np.int32)
+    offs = np.concatenate([s.P.offsets, s.N.offsets[1:] + s.P.offsets[-1]]).astype(np.int64)
+    dl = torch.from_numpy(letters).cuda()
+    decreasing = offs.copy()
+    decreasing[3] = decreasing[4] + 1          # offsets[3] > offsets[4]
+    shifted = offs.copy()
+    shifted[0] = 1                             # the first trace does not start at 0
+    with L.Context(workspace=ws, stop=L.STOP_NONE) as ctx:
+        for bad in (decreasing, shifted):
+            assert bad.max() <= len(letters)
+            with pytest.raises(L.LtlError) as e:
+                ctx.learn_device(dl, torch.from_numpy(bad).cuda(), s.P.n, s.N.n, s.max_len(), 2, max_size=6)
+            assert e.value.status == L.LTL_ERR_INVALID
+            assert "offsets decrease" in str(e.value)
+        got = ctx.learn_device(dl, torch.from_numpy(offs).cuda(), s.P.n, s.N.n, s.max_len(), 2, max_size=6)
+    want = O.learn(s.P, s.N, 2, max_size=6, stop_mode=0)
+    assert got["unique"][1:7] == want["unique"][1:7]
+    assert got["candidates"][1:7] == want["candidates"][1:7]
+
+
 def test_cache_entries_are_their_formulas_and_distinct(ws):
     """Every sampled cache entry: its rebuilt formula has the level's size and
     the oracle's characteristic matrix of that formula is the stored one; all

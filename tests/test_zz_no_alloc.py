@@ -79,3 +79,27 @@ def test_noalloc_trace_longer_than_max_len_within_its_words():
         torch.cuda.synchronize()
         got = d_out.cpu().numpy().view(np.uint64)
         assert np.array_equal(got, want), formula
+
+
+@pytest.mark.gpu
+def test_noalloc_rejects_decreasing_offsets_then_evaluates_exactly():
+    """Offsets that decrease: the pack kernel packs that trace as empty (no
+    letter of it is read) and flags the input, the call returns
+    LTL_ERR_INVALID; the next call with valid offsets is exact."""
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    ts = _rand_traces(11, 300, 2, 1, 40)
+    bad = ts.offsets.astype(np.int64).copy()
+    bad[5] = bad[6] + 1                        # offsets[5] > offsets[6], still inside the letters
+    assert bad.max() <= len(ts.letters)
+    d_letters = torch.from_numpy(ts.letters.astype(np.int32)).cuda()
+    d_out = torch.full((ts.n, 1), -1, dtype=torch.int64, device="cuda")
+    with pytest.raises(L.LtlError) as e:
+        L.evaluate_noalloc("F (p0 & X p1)", d_letters, torch.from_numpy(bad).cuda(), ts.n, 40, 2, d_out, 1)
+    assert e.value.status == L.LTL_ERR_INVALID
+    assert "offsets decrease" in str(e.value)
+    want = L.evaluate("F (p0 & X p1)", ts, 2, words_per_trace=1)
+    L.evaluate_noalloc("F (p0 & X p1)", d_letters, torch.from_numpy(ts.offsets.astype(np.int64)).cuda(), ts.n, 40,
+                       2, d_out, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(d_out.cpu().numpy().view(np.uint64), want)
