@@ -9,7 +9,10 @@ seven connectives; sizes 1..9, every level enumerated completely
 within a 32 GB memory budget.
 
 One step = one whole learn call (trace packing, then every size level's
-candidate kernel, reading back the control block after each level).
+candidate kernel, reading back the control block after each level).  Before
+the W warm-up steps the library's launch autotuner gets six untimed calls,
+one per launch configuration it tries; the warm-up and timed steps run the
+fastest configuration of every tuned launch class.
 
 Metric: candidates x traces per second = sum over completed size levels of
 (candidates built at that size) * |P u N|, divided by the step's device time.
