@@ -18,6 +18,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -1353,10 +1354,83 @@ public:
     }
 };
 
+// Host threads for large copies, started once per process: run(k, fn) calls
+// fn(0..k-1), one part on the calling thread and the others on the pool, and
+// returns when all are done.  Callers of run() take turns.  The pool is never
+// torn down (its idle threads wait on a condition variable; at process exit
+// they are simply ended), so no exit path waits on it.
+class CopyPool {
+public:
+    static CopyPool &get() {
+        static CopyPool *p = new CopyPool();
+        return *p;
+    }
+    int workers() const { return (int)n_workers; }
+    template <class F>
+    void run(int k, const F &fn) {
+        std::lock_guard<std::mutex> turn(run_mu);
+        std::function<void(int)> f(fn);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            job = &f;
+            n_parts = k;
+            next = 1;   // part 0 is the caller's
+            left = k;
+            ++gen;
+        }
+        cv.notify_all();
+        f(0);
+        take_parts();
+        std::unique_lock<std::mutex> lk(mu);
+        if (--left > 0) cv_done.wait(lk, [&] { return left == 0; });
+        job = nullptr;
+    }
+
+private:
+    CopyPool() {
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        n_workers = std::min(7u, hw > 1 ? hw - 1 : 0u);
+        for (unsigned i = 0; i < n_workers; ++i) std::thread([this] { loop(); }).detach();
+    }
+    // parts not yet started, taken by whichever thread is free
+    void take_parts() {
+        for (;;) {
+            int i;
+            const std::function<void(int)> *f;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                if (!job || next >= n_parts) return;
+                i = next++;
+                f = job;
+            }
+            (*f)(i);
+            std::lock_guard<std::mutex> lk(mu);
+            if (--left == 0) cv_done.notify_all();
+        }
+    }
+    void loop() {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return gen != seen; });
+                seen = gen;
+            }
+            take_parts();
+        }
+    }
+    unsigned n_workers = 0;
+    std::mutex run_mu, mu;
+    std::condition_variable cv, cv_done;
+    const std::function<void(int)> *job = nullptr;
+    int n_parts = 0, next = 0, left = 0;
+    uint64_t gen = 0;
+};
+
 // A host copy of n elements (at least one, zero when n is 0).  Large inputs
-// are copied by several threads, each of which also first-touches its share
-// of the fresh, uninitialised allocation: one thread copying a request of
-// 15 MB took about 1 ms, most of it page faults.
+// are copied in parts on the copy pool, each part's thread also
+// first-touching its share of the fresh, uninitialised allocation: one thread
+// copying a request of 15 MB took about 1 ms, most of it page faults.
 template <class T>
 std::unique_ptr<T[]> copy_parallel(const T *src, uint64_t n) {
     std::unique_ptr<T[]> dst(new (std::nothrow) T[n ? n : 1]);
@@ -1366,21 +1440,18 @@ std::unique_ptr<T[]> copy_parallel(const T *src, uint64_t n) {
         return dst;
     }
     const uint64_t bytes = n * sizeof(T);
-    const uint64_t hw = std::max(1u, std::thread::hardware_concurrency());
-    const uint64_t k = std::min<uint64_t>(std::min<uint64_t>(8, hw), std::max<uint64_t>(1, bytes >> 21));
+    CopyPool &pool = CopyPool::get();
+    const uint64_t k = std::min<uint64_t>((uint64_t)pool.workers() + 1, std::max<uint64_t>(1, bytes >> 21));
     if (k <= 1) {
         memcpy(dst.get(), src, bytes);
         return dst;
     }
     const uint64_t per = (n + k - 1) / k;
-    std::vector<std::thread> th;
     T *d = dst.get();
-    for (uint64_t i = 0; i < k; ++i) {
-        const uint64_t b = i * per, e = std::min(n, b + per);
-        if (b >= e) break;
-        th.emplace_back([d, src, b, e] { memcpy(d + b, src + b, (e - b) * sizeof(T)); });
-    }
-    for (auto &t : th) t.join();
+    pool.run((int)k, [d, src, n, per](int i) {
+        const uint64_t b = (uint64_t)i * per, e = std::min(n, b + per);
+        if (b < e) memcpy(d + b, src + b, (e - b) * sizeof(T));
+    });
     return dst;
 }
 
