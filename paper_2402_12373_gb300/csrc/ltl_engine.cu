@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -158,6 +159,64 @@ constexpr size_t kWsSmemMax = 224 * 1024;
 // A problem's round of at least this many candidates runs the
 // warp-specialised kernel under LTL_KERNEL_AUTO (when its shape has one).
 constexpr uint64_t kWsAutoMin = 1ull << 15;
+
+// Page-locked host blocks outlive the engines that use them.  Pinning costs
+// tens of microseconds per call plus time per page (the 64 MiB staging buffer
+// milliseconds), more than a small ltl_learn_batch call's own work, and every
+// such call builds an engine of its own.  So a block an engine releases goes
+// to the free list of its size class (powers of two from 4 KiB) and the next
+// engine takes it from there; blocks are never returned to the driver, so the
+// cache holds at most what the engines alive at one time held.  An engine
+// releases its blocks only after synchronising the stream their copies ran on.
+class PinnedCache {
+public:
+    static PinnedCache &get() {
+        static PinnedCache *c = new PinnedCache();
+        return *c;
+    }
+    cudaError_t alloc(void **p, size_t bytes) {
+        const int cls = size_class(bytes);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            std::vector<void *> &fl = free_list[cls];
+            if (!fl.empty()) {
+                *p = fl.back();
+                fl.pop_back();
+                return cudaSuccess;
+            }
+        }
+        const cudaError_t e = cudaMallocHost(p, (size_t)1 << cls);
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(mu);
+            class_of[*p] = cls;
+        }
+        return e;
+    }
+    void release(void *p) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        free_list[class_of.at(p)].push_back(p);
+    }
+
+private:
+    static int size_class(size_t bytes) {
+        int c = 12;
+        while (((size_t)1 << c) < bytes) ++c;
+        return c;
+    }
+    std::mutex mu;
+    std::map<void *, int> class_of;
+    std::vector<void *> free_list[64];
+};
+
+template <class T>
+cudaError_t pinned_alloc(T **p, size_t bytes) {
+    void *v = nullptr;
+    const cudaError_t e = PinnedCache::get().alloc(&v, bytes);
+    *p = (T *)v;
+    return e;
+}
+
 // Shared memory one CTA of the cluster kernel may hold its slice in.
 constexpr size_t kClusterSliceMax = 200 * 1024;
 
@@ -311,6 +370,7 @@ public:
     bool keep_finished = false;   // contexts keep the last problem for introspection
     // shared region at the start of the workspace
     size_t o_probs = 0, o_ctrls = 0, o_segs = 0, o_counters = 0, o_jobs = 0, o_tokens = 0, o_ntok = 0, shared_end = 0;
+    int probs_lo = INT32_MAX, probs_hi = -1;   // slots whose descriptors await upload
     size_t o_plan_state = 0, o_plan_log = 0, o_descs = 0;   // device planning of small levels
     PlanState *h_plan_state = nullptr;
     PlanLog *h_plan_log = nullptr;
@@ -410,15 +470,15 @@ public:
         o_tokens = take(sizeof(uint32_t) * kMaxTokens * max_slots);
         o_ntok = take(sizeof(int) * max_slots);
         shared_end = cur;
-        LTL_CUDA_TRY(cudaMallocHost(&h_probs, sizeof(Problem) * max_slots));
-        LTL_CUDA_TRY(cudaMallocHost(&h_ctrls, sizeof(Ctrl) * max_slots));
-        LTL_CUDA_TRY(cudaMallocHost(&h_staged, sizeof(unsigned long long) * kMaxGroups));
-        LTL_CUDA_TRY(cudaMallocHost(&h_segs, sizeof(Seg) * max_segs));
-        LTL_CUDA_TRY(cudaMallocHost(&h_jobs, sizeof(WalkJob) * max_slots));
-        LTL_CUDA_TRY(cudaMallocHost(&h_tokens, sizeof(uint32_t) * kMaxTokens * max_slots));
-        LTL_CUDA_TRY(cudaMallocHost(&h_ntok, sizeof(int) * max_slots));
-        LTL_CUDA_TRY(cudaMallocHost(&h_plan_state, sizeof(PlanState)));
-        LTL_CUDA_TRY(cudaMallocHost(&h_plan_log, sizeof(PlanLog) * kMaxLevels));
+        LTL_CUDA_TRY(pinned_alloc(&h_probs, sizeof(Problem) * max_slots));
+        LTL_CUDA_TRY(pinned_alloc(&h_ctrls, sizeof(Ctrl) * max_slots));
+        LTL_CUDA_TRY(pinned_alloc(&h_staged, sizeof(unsigned long long) * kMaxGroups));
+        LTL_CUDA_TRY(pinned_alloc(&h_segs, sizeof(Seg) * max_segs));
+        LTL_CUDA_TRY(pinned_alloc(&h_jobs, sizeof(WalkJob) * max_slots));
+        LTL_CUDA_TRY(pinned_alloc(&h_tokens, sizeof(uint32_t) * kMaxTokens * max_slots));
+        LTL_CUDA_TRY(pinned_alloc(&h_ntok, sizeof(int) * max_slots));
+        LTL_CUDA_TRY(pinned_alloc(&h_plan_state, sizeof(PlanState)));
+        LTL_CUDA_TRY(pinned_alloc(&h_plan_log, sizeof(PlanLog) * kMaxLevels));
         LTL_CUDA_TRY(cudaEventCreate(&ev_begin));
         LTL_CUDA_TRY(cudaEventCreate(&ev_end));
         slots.resize(max_slots);
@@ -440,16 +500,16 @@ public:
             else cudaFree(ws);
         }
         ws = nullptr;
-        if (h_probs) cudaFreeHost(h_probs);
-        if (h_ctrls) cudaFreeHost(h_ctrls);
-        if (h_staged) cudaFreeHost(h_staged);
-        if (h_segs) cudaFreeHost(h_segs);
-        if (h_jobs) cudaFreeHost(h_jobs);
-        if (h_tokens) cudaFreeHost(h_tokens);
-        if (h_ntok) cudaFreeHost(h_ntok);
-        if (h_plan_state) cudaFreeHost(h_plan_state);
-        if (h_plan_log) cudaFreeHost(h_plan_log);
-        if (h_pin) cudaFreeHost(h_pin);
+        PinnedCache::get().release(h_probs);
+        PinnedCache::get().release(h_ctrls);
+        PinnedCache::get().release(h_staged);
+        PinnedCache::get().release(h_segs);
+        PinnedCache::get().release(h_jobs);
+        PinnedCache::get().release(h_tokens);
+        PinnedCache::get().release(h_ntok);
+        PinnedCache::get().release(h_plan_state);
+        PinnedCache::get().release(h_plan_log);
+        PinnedCache::get().release(h_pin);
         h_pin = nullptr;
         h_probs = nullptr; h_ctrls = nullptr; h_staged = nullptr; h_segs = nullptr; h_jobs = nullptr; h_tokens = nullptr; h_ntok = nullptr;
         h_plan_state = nullptr; h_plan_log = nullptr;
@@ -619,13 +679,17 @@ public:
             uint32_t *dl = (uint32_t *)(base + L.o_letters);
             uint64_t *dof = (uint64_t *)(base + L.o_offsets);
             const uint64_t np = s.in.ho[0][s.in.hn[0]], nn = s.in.ho[1][s.in.hn[1]];
-            const size_t lb = round_up(4 * (np + nn), 256), need = lb + round_up(8 * (T + 1), 256);
+            // the staged letters and offsets sit as they do in the layout
+            // (offsets at the letters' size rounded up to 256 bytes), so one
+            // copy moves both
+            const size_t lb = round_up(4 * std::max<uint64_t>(np + nn, 1), 256),
+                         need = lb + round_up(8 * (T + 1), 256);
             if (need <= kPinStageMax) {
                 if (!h_pin || pin_head + need > kPinStageBytes) {
                     // every earlier staged upload has landed before the buffer is reused
                     LTL_CUDA_TRY(cudaStreamSynchronize(stream));
                     pin_head = 0;
-                    if (!h_pin) LTL_CUDA_TRY(cudaMallocHost(&h_pin, kPinStageBytes));
+                    if (!h_pin) LTL_CUDA_TRY(pinned_alloc(&h_pin, kPinStageBytes));
                 }
                 uint32_t *pl = (uint32_t *)(h_pin + pin_head);
                 uint64_t *po = (uint64_t *)(h_pin + pin_head + lb);
@@ -633,8 +697,13 @@ public:
                 if (nn) memcpy(pl + np, s.in.hl[1], 4 * nn);
                 for (uint64_t i = 0; i <= s.in.hn[0]; ++i) po[i] = s.in.ho[0][i];
                 for (uint64_t i = 1; i <= s.in.hn[1]; ++i) po[s.in.hn[0] + i] = np + s.in.ho[1][i];
-                if (np + nn) LTL_CUDA_TRY(cudaMemcpyAsync(dl, pl, 4 * (np + nn), cudaMemcpyHostToDevice, stream));
-                LTL_CUDA_TRY(cudaMemcpyAsync(dof, po, 8 * (T + 1), cudaMemcpyHostToDevice, stream));
+                if ((char *)dof == (char *)dl + lb) {
+                    LTL_CUDA_TRY(cudaMemcpyAsync(dl, pl, lb + 8 * (T + 1), cudaMemcpyHostToDevice, stream));
+                    s.st.h2d_bytes += lb - 4 * (np + nn);   // the padding between letters and offsets
+                } else {
+                    if (np + nn) LTL_CUDA_TRY(cudaMemcpyAsync(dl, pl, 4 * (np + nn), cudaMemcpyHostToDevice, stream));
+                    LTL_CUDA_TRY(cudaMemcpyAsync(dof, po, 8 * (T + 1), cudaMemcpyHostToDevice, stream));
+                }
                 pin_head += need;
             } else {
                 std::vector<uint64_t> offv(T + 1);
@@ -653,14 +722,15 @@ public:
         uint64_t *d_keys = (uint64_t *)(base + L.o_keys);
         uint64_t *d_atoms = (uint64_t *)(base + L.o_atoms);
         LTL_CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
-        LTL_CUDA_TRY(cudaMemsetAsync(base + L.o_hslots, 0, sizeof(HSlot) * L.hslots, stream));
-        // the pack kernel writes every word of the mask, the atoms and the NH keys
+        // the pack launch writes every word of the mask, the atoms and the NH
+        // keys, and clears the hash slots
+        void *d_hslots = base + L.o_hslots;
         if (L.narrow)
             LTL_CUDA_TRY(launch_pack_narrow(d_letters, d_offsets, (uint32_t)T, L.plane, L.n_props, d_mask, d_atoms,
-                                            L.stride, d_ctrl, stream, d_keys, kKeySeed));
+                                            L.stride, d_ctrl, stream, d_keys, kKeySeed, d_hslots, L.hslots));
         else
             LTL_CUDA_TRY(launch_pack(d_letters, d_offsets, (uint32_t)T, L.plane, L.W, L.Wt, L.n_props, d_mask, d_atoms,
-                                     L.stride, d_ctrl, stream, d_keys, kKeySeed));
+                                     L.stride, d_ctrl, stream, d_keys, kKeySeed, d_hslots, L.hslots));
         s.st.launches += 1;
         Problem &pb = h_probs[si];
         pb = Problem{};
@@ -690,8 +760,9 @@ public:
         pb.fkp_b = (uint32_t)std::max<uint64_t>(1, 63 / std::max<uint64_t>(T, 1));
         pb.key_mask = kKey63 >> std::min<uint32_t>(opts.ruc_mask_bits, 62);
         pb.spin_limit = opts.spin_limit ? opts.spin_limit : (1ull << 20);
-        LTL_CUDA_TRY(cudaMemcpyAsync((Problem *)(ws + o_probs) + si, &h_probs[si], sizeof(Problem),
-                                     cudaMemcpyHostToDevice, stream));
+        // uploaded with the others admitted before the next round (flush_probs)
+        probs_lo = std::min(probs_lo, si);
+        probs_hi = std::max(probs_hi, si);
         s.st.n_traces = T;
         s.st.words_per_trace = (uint32_t)L.W;
         s.st.threads_per_cta = (uint32_t)L.block;   // with the hash warps of the warp-specialised kernel
@@ -1009,7 +1080,24 @@ public:
     }
 
     // One round: the next size level of every running problem.
+    // The descriptors of the problems admitted since the last round, in one
+    // copy of the slot range they span (the slots between hold the
+    // descriptors of running or free slots, unchanged).
+    ltl_status flush_probs() {
+        if (probs_hi < probs_lo) return LTL_OK;
+        LTL_CUDA_TRY(cudaMemcpyAsync((Problem *)(ws + o_probs) + probs_lo, &h_probs[probs_lo],
+                                     sizeof(Problem) * (size_t)(probs_hi - probs_lo + 1), cudaMemcpyHostToDevice,
+                                     stream));
+        probs_lo = INT32_MAX;
+        probs_hi = -1;
+        return LTL_OK;
+    }
+
     ltl_status round() {
+        {
+            const ltl_status fs = flush_probs();
+            if (fs != LTL_OK) return fs;
+        }
         Costs cost;
         // 0 reads as 1; anything above the largest level only bans the connective
         for (int i = 0; i < 8; ++i)

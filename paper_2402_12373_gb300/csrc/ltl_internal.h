@@ -86,13 +86,17 @@ inline const void *fused_kernel_ptr(int W, int C, int op) {
 
 // Trace packing: traces of at most 64 * W positions into Wt >= W words each
 // (all Wt planes written); with `keys` also the NH fingerprint keys of `seed`,
-// one per matrix word (Wt * plane words, the stride of one matrix).
+// one per matrix word (Wt * plane words, the stride of one matrix); with
+// `zero` (16-byte aligned) the same launch also clears n_zero16 16-byte units
+// there.
 cudaError_t launch_pack(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane, int W,
                         int Wt, int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
-                        cudaStream_t s, uint64_t *keys = nullptr, uint64_t seed = 0);
+                        cudaStream_t s, uint64_t *keys = nullptr, uint64_t seed = 0, void *zero = nullptr,
+                        uint64_t n_zero16 = 0);
 cudaError_t launch_pack_narrow(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
                                int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
-                               cudaStream_t s, uint64_t *keys = nullptr, uint64_t seed = 0);
+                               cudaStream_t s, uint64_t *keys = nullptr, uint64_t seed = 0, void *zero = nullptr,
+                               uint64_t n_zero16 = 0);
 cudaError_t launch_walk_batch(const WalkJob *jobs, int n_jobs, uint32_t *tokens, int cap, int *n_out, cudaStream_t s);
 struct PlanArgs;
 cudaError_t launch_plan(const PlanArgs &a, int k, bool close_prev, bool plan_this, cudaStream_t s);

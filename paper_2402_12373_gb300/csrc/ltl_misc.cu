@@ -3,6 +3,8 @@
 // that rebuilds a formula, formula evaluation (ltl_eval) and the launchers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "ltl_device.cuh"
@@ -15,7 +17,8 @@ namespace ltl {
 // given `keys`, the NH fingerprint keys, one per matrix word).  One thread per
 // (plane w < Wt, trace slot t); every word of the mask, the atoms and the keys
 // is written, the padding planes W..Wt-1 as zeros, so none needs clearing
-// first.  Positions are read straight from the
+// first.  Given `zero`, the launch also clears n_zero 16-byte units there
+// (a problem's hash slots), grid-stride over all its threads.  Positions are read straight from the
 // concatenated letters; a letter with a bit >= n_props, a decreasing offset
 // or a trace longer than 64 * W marks the input invalid (a trace with bad
 // offsets is then packed as empty).
@@ -28,8 +31,10 @@ __device__ __forceinline__ uint64_t nh_key(uint64_t seed, uint64_t i) {
 
 __global__ void pack_kernel(const uint32_t *__restrict__ letters, const uint64_t *__restrict__ offsets,
                             uint32_t n_traces, uint64_t plane, int W, int Wt, int n_props, uint64_t *mask,
-                            uint64_t *atoms, uint64_t stride, Ctrl *ctrl, uint64_t *keys, uint64_t seed) {
+                            uint64_t *atoms, uint64_t stride, Ctrl *ctrl, uint64_t *keys, uint64_t seed,
+                            uint4 *zero, uint64_t n_zero) {
     const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t i = idx; i < n_zero; i += (uint64_t)gridDim.x * blockDim.x) zero[i] = make_uint4(0, 0, 0, 0);
     if (idx >= plane * (uint64_t)Wt) return;
     if (keys) keys[idx] = nh_key(seed, idx);
     const uint64_t t = idx % plane, w = idx / plane;
@@ -68,8 +73,10 @@ __global__ void pack_kernel(const uint32_t *__restrict__ letters, const uint64_t
 // 2q (bits 0..31) and 2q + 1 (bits 32..63).  One thread per word.
 __global__ void pack_narrow_kernel(const uint32_t *__restrict__ letters, const uint64_t *__restrict__ offsets,
                                    uint32_t n_traces, uint64_t plane, int n_props, uint64_t *mask, uint64_t *atoms,
-                                   uint64_t stride, Ctrl *ctrl, uint64_t *keys, uint64_t seed) {
+                                   uint64_t stride, Ctrl *ctrl, uint64_t *keys, uint64_t seed, uint4 *zero,
+                                   uint64_t n_zero) {
     const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t i = q; i < n_zero; i += (uint64_t)gridDim.x * blockDim.x) zero[i] = make_uint4(0, 0, 0, 0);
     if (q >= plane) return;
     if (keys) keys[q] = nh_key(seed, q);
     uint64_t off[2] = {0, 0}, len[2] = {0, 0};
@@ -223,22 +230,32 @@ __global__ void unpack_kernel(const uint64_t *src, uint64_t plane, int W, uint32
 // Host-callable launchers
 // ---------------------------------------------------------------------------
 
+// CTAs of a pack launch: enough for its words, and for clearing n_zero
+// 16-byte units at about four per thread (at most 4096 CTAs; the clearing
+// loop is grid-stride).
+static unsigned pack_blocks(uint64_t units, uint64_t n_zero, int th) {
+    const uint64_t b_pack = (units + th - 1) / th;
+    const uint64_t b_zero = std::min<uint64_t>((n_zero + 4ull * th - 1) / (4ull * th), 4096);
+    return (unsigned)std::max<uint64_t>(std::max(b_pack, b_zero), 1);
+}
+
 cudaError_t launch_pack(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
                         int W, int Wt, int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
-                        cudaStream_t s, uint64_t *keys, uint64_t seed) {
-    const uint64_t n = plane * (uint64_t)Wt;
+                        cudaStream_t s, uint64_t *keys, uint64_t seed, void *zero, uint64_t n_zero16) {
     const int th = 256;
-    pack_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>(letters, offsets, n_traces, plane, W, Wt, n_props,
-                                                             mask, atoms, stride, ctrl, keys, seed);
+    pack_kernel<<<pack_blocks(plane * (uint64_t)Wt, zero ? n_zero16 : 0, th), th, 0, s>>>(
+        letters, offsets, n_traces, plane, W, Wt, n_props, mask, atoms, stride, ctrl, keys, seed, (uint4 *)zero,
+        zero ? n_zero16 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_narrow(const uint32_t *letters, const uint64_t *offsets, uint32_t n_traces, uint64_t plane,
                                int n_props, uint64_t *mask, uint64_t *atoms, uint64_t stride, Ctrl *ctrl,
-                               cudaStream_t s, uint64_t *keys, uint64_t seed) {
+                               cudaStream_t s, uint64_t *keys, uint64_t seed, void *zero, uint64_t n_zero16) {
     const int th = 256;
-    pack_narrow_kernel<<<(unsigned)((plane + th - 1) / th), th, 0, s>>>(letters, offsets, n_traces, plane, n_props,
-                                                                        mask, atoms, stride, ctrl, keys, seed);
+    pack_narrow_kernel<<<pack_blocks(plane, zero ? n_zero16 : 0, th), th, 0, s>>>(
+        letters, offsets, n_traces, plane, n_props, mask, atoms, stride, ctrl, keys, seed, (uint4 *)zero,
+        zero ? n_zero16 : 0);
     return cudaGetLastError();
 }
 
