@@ -94,26 +94,24 @@ class Stats(ctypes.Structure):
                 ("op_alone", (ctypes.c_uint8 * 8) * MAX_LEVELS)]
 
     def to_dict(self, max_size: int) -> Dict:
+        # ctypes scalar fields read as Python numbers, array slices as lists
         K = max_size
         return {
             "levels_done": self.levels_done, "found_size": self.found_size,
-            "unique": [int(self.unique[c]) for c in range(K + 1)],
-            "candidates": [int(self.candidates[c]) for c in range(K + 1)],
-            "ms": [float(self.ms[c]) for c in range(K + 1)],
-            "entries": int(self.entries), "n_traces": int(self.n_traces),
-            "words_per_trace": int(self.words_per_trace), "threads_per_cta": int(self.threads_per_cta),
-            "traces_per_thread": int(self.traces_per_thread), "chunk_groups": int(self.chunk_groups),
-            "batch": int(self.batch), "ctas_per_sm": int(self.ctas_per_sm),
-            "traces_per_word": int(self.traces_per_word),
-            "launches": int(self.launches), "h2d_bytes": int(self.h2d_bytes),
-            "d2h_bytes": int(self.d2h_bytes), "max_entries": int(self.max_entries),
-            "total_ms": float(self.total_ms),
-            "op_ms": [[float(self.op_ms[c][o]) for o in range(8)] for c in range(K + 1)],
-            "device_planned_levels": int(self.device_planned_levels), "graph_levels": int(self.graph_levels),
-            "compares": int(self.compares), "collisions": int(self.collisions),
-            "op_staged": [[int(self.op_staged[c][o]) for o in range(8)] for c in range(K + 1)],
-            "op_kernel": [[LAUNCH_KINDS[int(self.op_kernel[c][o])] for o in range(8)] for c in range(K + 1)],
-            "op_alone": [[bool(self.op_alone[c][o]) for o in range(8)] for c in range(K + 1)],
+            "unique": self.unique[:K + 1], "candidates": self.candidates[:K + 1], "ms": self.ms[:K + 1],
+            "entries": self.entries, "n_traces": self.n_traces,
+            "words_per_trace": self.words_per_trace, "threads_per_cta": self.threads_per_cta,
+            "traces_per_thread": self.traces_per_thread, "chunk_groups": self.chunk_groups,
+            "batch": self.batch, "ctas_per_sm": self.ctas_per_sm, "traces_per_word": self.traces_per_word,
+            "launches": self.launches, "h2d_bytes": self.h2d_bytes,
+            "d2h_bytes": self.d2h_bytes, "max_entries": self.max_entries,
+            "total_ms": self.total_ms,
+            "op_ms": [self.op_ms[c][:] for c in range(K + 1)],
+            "device_planned_levels": self.device_planned_levels, "graph_levels": self.graph_levels,
+            "compares": self.compares, "collisions": self.collisions,
+            "op_staged": [self.op_staged[c][:] for c in range(K + 1)],
+            "op_kernel": [[LAUNCH_KINDS[x] for x in self.op_kernel[c][:]] for c in range(K + 1)],
+            "op_alone": [[x != 0 for x in self.op_alone[c][:]] for c in range(K + 1)],
         }
 
 
@@ -130,12 +128,13 @@ class Result(ctypes.Structure):
                 ("latency_ms", ctypes.c_double)]
 
     def to_dict(self) -> Dict:
-        st = int(self.status)
-        return {"id": int(self.id), "status": STATUS.get(st, st), "size": int(self.found_size) if st == 0 else None,
-                "formula": self.formula.decode() if st == 0 else None, "levels_done": int(self.levels_done),
-                "unique": [int(x) for x in self.unique], "candidates": [int(x) for x in self.candidates],
-                "n_traces": int(self.n_traces), "rounds": int(self.rounds), "queue_ms": float(self.queue_ms),
-                "latency_ms": float(self.latency_ms)}
+        # ctypes scalar fields read as Python numbers, array slices as lists
+        st = self.status
+        return {"id": self.id, "status": STATUS.get(st, st), "size": self.found_size if st == 0 else None,
+                "formula": self.formula.decode() if st == 0 else None, "levels_done": self.levels_done,
+                "unique": self.unique[:], "candidates": self.candidates[:],
+                "n_traces": self.n_traces, "rounds": self.rounds, "queue_ms": self.queue_ms,
+                "latency_ms": self.latency_ms}
 
 
 _lib = None

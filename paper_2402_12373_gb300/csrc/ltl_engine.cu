@@ -24,7 +24,9 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <set>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "ltl_autotune.h"
@@ -217,6 +219,25 @@ cudaError_t pinned_alloc(T **p, size_t bytes) {
     return e;
 }
 
+// Launch properties of the level kernels, shared by every engine of the
+// process: the opt-in to the device's shared-memory maximum, the carveout and
+// the permission for clusters of more than 8 CTAs are attributes of the
+// function, and the resident CTAs (or clusters) depend only on the function,
+// block size, shared memory, cluster size and device.  Queried again in every
+// engine they cost each ltl_learn_batch call (an engine of its own) tens of
+// CUDA calls.
+struct LaunchCache {
+    static LaunchCache &get() {
+        static LaunchCache *c = new LaunchCache();
+        return *c;
+    }
+    std::mutex mu;
+    std::map<std::tuple<int, const void *, int, size_t>, int> occ;           // resident CTAs per SM
+    std::map<std::pair<int, const void *>, int> dyn_max;                     // opted in: its dynamic smem maximum
+    std::set<std::pair<int, const void *>> nonportable;                      // clusters of 16 allowed
+    std::map<std::tuple<int, const void *, int, size_t, int>, int> clusters;   // resident clusters
+};
+
 // Shared memory one CTA of the cluster kernel may hold its slice in.
 constexpr size_t kClusterSliceMax = 200 * 1024;
 
@@ -392,26 +413,6 @@ public:
     size_t pin_head = 0;
     std::vector<Slot> slots;
     FreeList mem;
-    struct Occ {
-        const void *fn;
-        int nt;
-        size_t smem;
-        int blocks;
-    };
-    std::vector<Occ> occ;
-    std::vector<const void *> opted_in;
-    std::vector<const void *> nonportable;   // cluster kernels allowed clusters of more than 8 CTAs
-
-    int max_dynamic_smem(const void *fn) const {
-        int optin = 0;
-        cudaFuncAttributes fa;
-        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
-            cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return 0;
-        }
-        return optin - (int)fa.sharedSizeBytes;
-    }
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     std::vector<cudaEvent_t> ev_op;   // after each launch of a round, created on demand
     std::vector<cudaEvent_t> ev_chain;   // device-planned chains: per level, its start and each launch
@@ -595,40 +596,53 @@ public:
     // memory (opted in); cached.
     ltl_status occupancy(const void *fn, int nt, size_t smem, int &blocks) {
         if (!fn) return fail(LTL_ERR_INVALID, "no level kernel for this shape");
-        for (const auto &e : occ)
-            if (e.fn == fn && e.nt == nt && e.smem == smem) {
-                blocks = e.blocks;
-                return LTL_OK;
-            }
+        LaunchCache &lc = LaunchCache::get();
+        std::lock_guard<std::mutex> lk(lc.mu);
+        const auto key = std::make_tuple(device, fn, nt, smem);
+        const auto hit = lc.occ.find(key);
+        if (hit != lc.occ.end()) {
+            blocks = hit->second;
+            return LTL_OK;
+        }
         // the opt-in limit is an attribute of the function (the last setter
         // wins), so every level kernel is opted in once to the device maximum
-        if (std::find(opted_in.begin(), opted_in.end(), fn) == opted_in.end()) {
+        const auto fk = std::make_pair(device, fn);
+        auto dyn = lc.dyn_max.find(fk);
+        if (dyn == lc.dyn_max.end()) {
             int optin = 0;
             LTL_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
             cudaFuncAttributes fa;
             LTL_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
-            const int dyn = optin - (int)fa.sharedSizeBytes;
-            LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+            const int d = optin - (int)fa.sharedSizeBytes;
+            LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, d));
             // all of the unified L1 / shared storage as shared memory, so that
             // shared memory does not cap the resident CTAs below the registers
             LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-            opted_in.push_back(fn);
+            dyn = lc.dyn_max.emplace(fk, d).first;
         }
-        if ((long long)smem > (long long)max_dynamic_smem(fn))
+        if ((long long)smem > (long long)dyn->second)
             return fail(LTL_ERR_INVALID, "problem needs %zu bytes of shared memory per CTA", smem);
         int b = 0;
         LTL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, nt, smem));
         if (b < 1) return fail(LTL_ERR_INVALID, "level kernel cannot be resident (threads %d, smem %zu)", nt, smem);
-        occ.push_back({fn, nt, smem, b});
+        lc.occ.emplace(key, b);
         blocks = b;
         return LTL_OK;
     }
 
     // Clusters of `cl` CTAs of a cluster kernel that can be resident at once.
     ltl_status cluster_capacity(const void *fn, int nt, size_t smem, int cl, int &clusters) {
-        if (cl > 8 && std::find(nonportable.begin(), nonportable.end(), fn) == nonportable.end()) {
+        LaunchCache &lc = LaunchCache::get();
+        std::lock_guard<std::mutex> lk(lc.mu);
+        const auto key = std::make_tuple(device, fn, nt, smem, cl);
+        const auto hit = lc.clusters.find(key);
+        if (hit != lc.clusters.end()) {
+            clusters = hit->second;
+            return LTL_OK;
+        }
+        if (cl > 8 && !lc.nonportable.count(std::make_pair(device, fn))) {
             LTL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-            nonportable.push_back(fn);
+            lc.nonportable.insert(std::make_pair(device, fn));
         }
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -644,6 +658,7 @@ public:
         int n = 0;
         LTL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, fn, &cfg));
         if (n < 1) return fail(LTL_ERR_INVALID, "no cluster of %d CTAs can be resident (smem %zu)", cl, smem);
+        lc.clusters.emplace(key, n);
         clusters = n;
         return LTL_OK;
     }
@@ -1331,35 +1346,32 @@ public:
             LTL_CUDA_TRY(cudaEventElapsedTime(&since, ev_begin, ev_op[g]));
             round_ms = std::max(round_ms, since);
         }
+        // per problem and launch (a problem's segments of one connective are
+        // in one launch): the launch's time, kernel and staged operands, and
+        // the launch counted once for each problem it served -- one pass over
+        // the segments, before the levels are closed
+        std::vector<int> stamp(max_slots, -1);
+        for (size_t g = 0; g < groups.size(); ++g)
+            for (int i : groups[g].seg_ids) {
+                const int p = segs[i].prob;
+                if (stamp[p] == (int)g) continue;
+                stamp[p] = (int)g;
+                Slot &s = slots[p];
+                const int k = s.level, op = groups[g].op;
+                s.st.op_ms[k][op] = op_ms[g];
+                s.st.op_kernel[k][op] = (uint8_t)groups[g].kind;
+                s.st.op_alone[k][op] = (!concurrent && (!split || (int)g == lead)) ? 1 : 0;
+                s.st.op_staged[k][op] = h_staged[g];
+                s.st.launches += 1;
+            }
         // close the level of every problem that ran
         for (int si : ran) {
             Slot &s = slots[si];
             const Ctrl &h = h_ctrls[si];
-            const int k = s.level;
             s.rounds++;
-            s.st.ms[k] = round_ms;
-            for (size_t g = 0; g < groups.size(); ++g)
-                for (int i : groups[g].seg_ids)
-                    if (segs[i].prob == si) {
-                        s.st.op_ms[k][groups[g].op] = op_ms[g];
-                        s.st.op_kernel[k][groups[g].op] = (uint8_t)groups[g].kind;
-                        s.st.op_alone[k][groups[g].op] = (!concurrent && (!split || (int)g == lead)) ? 1 : 0;
-                        s.st.op_staged[k][groups[g].op] = h_staged[g];
-                        break;
-                    }
+            s.st.ms[s.level] = round_ms;
             s.st.d2h_bytes += sizeof(Ctrl) + sizeof(unsigned long long) * groups.size();
             close_level(si, h, found_slots);
-        }
-        // one launch per group was shared by its problems: count it once each
-        for (size_t g = 0; g < groups.size(); ++g) {
-            std::vector<int> seen;
-            for (int i : groups[g].seg_ids) {
-                const int p = segs[i].prob;
-                if (std::find(seen.begin(), seen.end(), p) == seen.end()) {
-                    seen.push_back(p);
-                    slots[p].st.launches += 1;
-                }
-            }
         }
         return rebuild_formulas(found_slots);
     }
