@@ -6,7 +6,9 @@
  * size-by-size enumeration over !, &, |, X, F, G and U (Section 3, the
  * `enum` / `handleOp` / check-and-cache steps), each formula represented by
  * its characteristic matrix of bit-vectors (Section 4), F, G and U computed
- * by exponential propagation in O(log n) shifts (Section 4, Appendix B), and
+ * branch-free -- by default as an integer carry chain over the bit-reversed
+ * trace, or (ltl_opts.propagation) by the paper's exponential propagation in
+ * O(log n) shifts (Section 4, Appendix B), with identical results -- and
  * every candidate deduplicated exactly by observational equivalence modulo the
  * suffixes of the input traces (Section 5 with an exact, not relaxed, check).
  *
@@ -32,6 +34,13 @@
  *    leaves the context usable; LTL_ERR_BUFSIZE reports a too-small output
  *    buffer (the required size is written where stated).
  *  - Threads.  A context may be used by one host thread at a time.
+ *  - Process-wide state.  The library keeps, for the life of the process,
+ *    page-locked host blocks that contexts, batches and servers release (the
+ *    next one reuses them instead of pinning memory again), the launch
+ *    properties of its kernels per device, and a few idle host threads for
+ *    copying large submitted inputs.  Do not reset a device
+ *    (cudaDeviceReset) while the library is loaded: the cached blocks and
+ *    properties belong to the device's context.
  */
 #ifndef LTL_GB300_H
 #define LTL_GB300_H

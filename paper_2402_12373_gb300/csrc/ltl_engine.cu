@@ -197,7 +197,12 @@ public:
     void release(void *p) {
         if (!p) return;
         std::lock_guard<std::mutex> lk(mu);
-        free_list[class_of.at(p)].push_back(p);
+        const auto it = class_of.find(p);
+        if (it == class_of.end()) {
+            cudaFreeHost(p);   // not a block of this cache
+            return;
+        }
+        free_list[it->second].push_back(p);
     }
 
 private:
